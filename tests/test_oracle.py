@@ -1,0 +1,331 @@
+"""Pins for the CPU oracle (no GPU).
+
+Each test checks the oracle against something other than itself: a closed
+form, brute-force enumeration, an independently assembled Newton system
+(Eq. (7)), linear-algebra invariants (K symmetric positive definite, Eq. (9)),
+finite differences, or the paper's printed settings.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+
+import oracle
+import qpgen
+from oracle import ipm as I
+from oracle.metrics import full_multipliers
+from tests.bruteforce import solve_bruteforce
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _random_interior_state(S, seed):
+    rng = np.random.default_rng(seed)
+    st = I.initial_point(S)
+    st.x = rng.uniform(-0.4, 0.4, S.n)
+    for k in ("s_lA", "s_uA", "s_lx", "s_ux", "lam_lA", "lam_uA", "lam_lx", "lam_ux"):
+        v = getattr(st, k)
+        setattr(st, k, np.exp(rng.uniform(-4, 2, len(v))))
+    st.lam_e = rng.standard_normal(len(st.lam_e))
+    return st
+
+
+def _tiny_problems():
+    out = []
+    for seed in range(4):
+        out.append(qpgen.tiny_qp(5, 3, seed, me=0))
+        out.append(qpgen.tiny_qp(5, 2, 100 + seed, me=1))
+        out.append(qpgen.tiny_qp(4, 3, 200 + seed, me=0, two_sided=False))
+    return out
+
+
+# ---------------------------------------------------------------- closed form
+@pytest.mark.parametrize("kind", ["dense", "csr_lsq"])
+def test_unconstrained_closed_form(kind):
+    """No A, C or bounds: x* = -H^{-1} p (section 2.1, Eq. (1) with no constraints)."""
+    if kind == "dense":
+        qp = qpgen.dense_qp(30, 1, seed=3)
+        qp.akind, qp.A, qp.lA, qp.uA = "none", None, None, None
+    else:
+        qp = qpgen.dose_qp(400, 40, 10, 12, 1, seed=5)
+        qp.akind, qp.a_rows, qp.lA, qp.uA = "none", None, None, None
+    qp.lx = np.full(qp.n, -np.inf)
+    qp.ux = np.full(qp.n, np.inf)
+    res = oracle.ipm_solve(qp)
+    H = qp.H_dense()
+    xstar = -np.linalg.solve(H, qp.p)
+    assert res.status == "converged"
+    assert np.max(np.abs(res.x - xstar)) <= 1e-10 * (1 + np.max(np.abs(xstar)))
+
+
+# ---------------------------------------------------------------- brute force
+@pytest.mark.parametrize("qp", _tiny_problems(), ids=lambda q: f"seed{q.meta['seed']}")
+def test_bruteforce_active_set(qp):
+    """IPM optimum equals the active-set enumeration optimum to O(mu_final)."""
+    res = oracle.ipm_solve(qp)
+    assert res.status == "converged"
+    H = qp.H_dense()
+    ref = solve_bruteforce(H, qp.p, qp.A, qp.lA, qp.uA, qp.C, qp.b, qp.lx, qp.ux)
+    assert ref is not None
+    xs, fs = ref
+    ftol = 1e-6 * (1 + abs(fs))
+    assert abs(qp.objective(res.x) - fs) <= ftol
+    # strict convexity: f(x) - f* >= lam_min(H)/2 ||x - x*||^2 for feasible x,
+    # so the objective gate bounds the distance (degenerate constraints make
+    # the central path approach x* like sqrt(mu), not mu)
+    lmin = np.min(np.linalg.eigvalsh(H))
+    assert np.linalg.norm(res.x - xs) <= np.sqrt(2 * ftol / lmin)
+    lA, uA, lx, ux, le = full_multipliers(res.scaled, res.lam, qp)
+    met = oracle.kkt_metrics(qp, res.x, lA, uA, lx, ux, le)
+    assert met["kkt_rel"] <= 1e-6
+
+
+def test_bruteforce_catches_planted_sign_error(monkeypatch):
+    """A planted mistake in the oracle (wrong sign of the A' lam term in r_H)
+    must be caught by the brute-force pin."""
+    qp = qpgen.tiny_qp(5, 3, 1, me=0)
+    H = qp.H_dense()
+    xs, _ = solve_bruteforce(H, qp.p, qp.A, qp.lA, qp.uA, qp.C, qp.b, qp.lx, qp.ux)
+    orig = I._ATy
+
+    def bad(S, yL, yU):
+        return -orig(S, yL, yU)
+    monkeypatch.setattr(I, "_ATy", bad)
+    res = oracle.ipm_solve(qp, maxit=60)
+    assert res.status != "converged" or np.max(np.abs(res.x - xs)) > 1e-4
+
+
+# ---------------------------------------------------------------- reductions
+@pytest.mark.parametrize("qp", _tiny_problems()[:6], ids=lambda q: f"seed{q.meta['seed']}")
+def test_newton_formulations_agree(qp):
+    """Eq. (7) (full, LU), Eq. (8) (LDL^T), Eq. (9) (Cholesky) and the Schur
+    form give the same Newton direction at random interior iterates."""
+    S = I.scale(qp)
+    for seed in range(3):
+        st = _random_interior_state(S, seed)
+        mu = 10.0 ** -seed
+        r = I.residuals(S, st, mu)
+        J, off = I.full_newton_matrix(S, st, mu)
+        sol = np.linalg.solve(J, I.full_newton_rhs(r))
+        dx_full = sol[off[0]:off[1]]
+        dl_full = np.concatenate([sol[off[5]:off[6]], sol[off[1]:off[2]], sol[off[2]:off[3]]])
+        dg, D, r1, r2 = I.reduced_system(S, st, r, mu)
+        dx1, dl1 = I.newton_direct(S, dg, D, r1, r2, "ldl")
+        dx2, dl2 = I.newton_direct(S, dg, D, r1, r2, "schur_dense")
+        K = I.doubly_augmented_matrix(S, dg, D)
+        z = sla.cho_solve(sla.cho_factor(K), I.doubly_augmented_rhs(S, D, r1, r2))
+        scale = 1 + np.max(np.abs(sol))
+        for dx, dl in ((dx1, dl1), (dx2, dl2), (z[:S.n], z[S.n:])):
+            assert np.max(np.abs(dx - dx_full)) <= 1e-9 * scale
+            assert np.max(np.abs(dl - dl_full)) <= 1e-9 * scale
+        # full-system slack / bound-multiplier parts equal the recovery formulas
+        d = I.recover_step(S, st, r, dx1, dl1)
+        for blk, key in ((6, "s_lA"), (7, "s_uA"), (8, "s_lx"), (9, "s_ux"),
+                         (3, "lam_lx"), (4, "lam_ux")):
+            assert np.max(np.abs(sol[off[blk]:off[blk + 1]] - d[key]), initial=0) <= 1e-8 * scale
+
+
+def test_reduction_catches_planted_dropped_term(monkeypatch):
+    """Dropping the S_lx^-1 r_c3 term of r1 (Eq. (8)) is caught by the
+    comparison against the independently assembled Eq. (7)."""
+    qp = qpgen.tiny_qp(5, 3, 2, me=0)
+    S = I.scale(qp)
+    st = _random_interior_state(S, 7)
+    mu = 0.1
+    r = I.residuals(S, st, mu)
+    J, off = I.full_newton_matrix(S, st, mu)
+    dx_full = np.linalg.solve(J, I.full_newton_rhs(r))[:S.n]
+    orig = I.reduced_system
+
+    def bad(S_, st_, r_, mu_):
+        dg, D, r1, r2 = orig(S_, st_, r_, mu_)
+        r1 = r1.copy()
+        r1[S_.Lx] += r_["r_c3"] / st_.s_lx
+        return dg, D, r1, r2
+    monkeypatch.setattr(I, "reduced_system", bad)
+    dg, D, r1, r2 = I.reduced_system(S, st, r, mu)
+    dx, _ = I.newton_direct(S, dg, D, r1, r2, "ldl")
+    assert np.max(np.abs(dx - dx_full)) > 1e-6
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_K_symmetric_positive_definite(seed):
+    """Eq. (9) is SPD for convex problems (section 3.1)."""
+    qp = qpgen.tiny_qp(6, 4, 300 + seed, me=1)
+    S = I.scale(qp)
+    st = _random_interior_state(S, seed)
+    r = I.residuals(S, st, 1e-3)
+    dg, D, _, _ = I.reduced_system(S, st, r, 1e-3)
+    K = I.doubly_augmented_matrix(S, dg, D)
+    assert np.allclose(K, K.T, atol=1e-13 * np.abs(K).max(), rtol=0)
+    sla.cholesky(K)          # raises if not SPD
+    assert np.min(np.linalg.eigvalsh(K)) > 0
+
+
+@pytest.mark.parametrize("maker", [
+    lambda: qpgen.tiny_qp(6, 4, 11, me=1),
+    lambda: qpgen.dose_qp(300, 40, 8, 10, 12, seed=12),
+    lambda: qpgen.svm_qp(60, 5, seed=13),
+], ids=["dense", "csr_lsq", "lowrank"])
+def test_matrix_free_apply_and_diag(maker):
+    qp = maker()
+    S = I.scale(qp)
+    st = _random_interior_state(S, 3)
+    r = I.residuals(S, st, 0.01)
+    dg, D, _, _ = I.reduced_system(S, st, r, 0.01)
+    K = I.doubly_augmented_matrix(S, dg, D)
+    v = np.random.default_rng(0).standard_normal(K.shape[0])
+    assert np.allclose(I.kkt_apply(S, dg, D, v), K @ v, rtol=1e-12, atol=1e-12 * np.abs(K).max())
+    assert np.allclose(I.jacobi_diagonal(S, dg, D), np.diag(K), rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("maker,solver", [
+    (lambda: qpgen.dose_qp(600, 80, 12, 15, 30, seed=21), "schur_banded"),
+    (lambda: qpgen.svm_qp(120, 6, seed=22), "schur_woodbury"),
+    (lambda: qpgen.dense_qp(40, 20, seed=23), "schur_dense"),
+])
+def test_structured_direct_solvers(maker, solver):
+    qp = maker()
+    S = I.scale(qp)
+    st = _random_interior_state(S, 5)
+    r = I.residuals(S, st, 0.01)
+    dg, D, r1, r2 = I.reduced_system(S, st, r, 0.01)
+    dx0, dl0 = I.newton_direct(S, dg, D, r1, r2, "ldl")
+    dx1, dl1 = I.newton_direct(S, dg, D, r1, r2, solver)
+    sc = 1 + np.max(np.abs(np.concatenate([dx0, dl0])))
+    assert np.max(np.abs(dx1 - dx0)) <= 1e-8 * sc
+    assert np.max(np.abs(dl1 - dl0)) <= 1e-8 * sc
+
+
+def test_pcg_reference_matches_direct():
+    qp = qpgen.tiny_qp(6, 4, 31, me=1)
+    S = I.scale(qp)
+    st = _random_interior_state(S, 1)
+    r = I.residuals(S, st, 0.1)
+    dg, D, r1, r2 = I.reduced_system(S, st, r, 0.1)
+    K = I.doubly_augmented_matrix(S, dg, D)
+    rhs = I.doubly_augmented_rhs(S, D, r1, r2)
+    z, it, tres = I.pcg_reference(lambda v: K @ v, rhs, np.diag(K), 1e-12, 500)
+    zs = np.linalg.solve(K, rhs)
+    assert tres <= 1e-11
+    assert np.max(np.abs(z - zs)) <= 1e-9 * (1 + np.max(np.abs(zs)))
+
+
+def test_ratio_test_closed_form():
+    """Eq. (10) on hand-made values."""
+    st = I.State(x=np.zeros(1), s_lA=np.array([1.0, 2.0]), s_uA=np.array([4.0]),
+                 s_lx=np.zeros(0), s_ux=np.zeros(0), lam_e=np.zeros(0),
+                 lam_lA=np.array([1.0, 1.0]), lam_uA=np.array([3.0]),
+                 lam_lx=np.zeros(0), lam_ux=np.zeros(0))
+    d = {"s_lA": np.array([-4.0, 1.0]), "s_uA": np.array([-2.0]), "s_lx": np.zeros(0),
+         "s_ux": np.zeros(0), "lam_lA": np.array([0.5, 0.5]), "lam_uA": np.array([-1.0]),
+         "lam_lx": np.zeros(0), "lam_ux": np.zeros(0)}
+    ax, al = I.ratio_test(st, d, 0.99)
+    assert ax == pytest.approx(0.99 * 0.25)
+    assert al == 1.0        # 0.99 * 3 > 1
+    d["s_lA"][:] = 1.0
+    d["s_uA"][:] = 0.0
+    ax, _ = I.ratio_test(st, d, 0.99)
+    assert ax == 1.0        # empty set
+
+
+# ---------------------------------------------------------------- adjoint
+def test_adjoint_unconstrained_equals_minus_Hinv():
+    qp = qpgen.dense_qp(20, 1, seed=41)
+    qp.akind, qp.A, qp.lA, qp.uA = "none", None, None, None
+    qp.lx = np.full(qp.n, -np.inf)
+    qp.ux = np.full(qp.n, np.inf)
+    res = oracle.ipm_solve(qp)
+    g = np.random.default_rng(1).standard_normal(qp.n)
+    adj = oracle.adjoint_solve(res.scaled, res.state, res.mu, g)
+    ref = -np.linalg.solve(qp.H_dense(), g)
+    assert np.max(np.abs(adj["p"] - ref)) <= 1e-9 * (1 + np.max(np.abs(ref)))
+
+
+def test_adjoint_active_set_limit():
+    """With a known active set the mu -> 0 derivative is -N (N'HN)^-1 N' g."""
+    qp = qpgen.tiny_qp(5, 3, 2, me=0)
+    res = oracle.ipm_solve(qp)
+    H = qp.H_dense()
+    x = res.x
+    act = []
+    for i in range(qp.m):
+        v = qp.A[i] @ x
+        if abs(v - qp.lA[i]) < 1e-5 or abs(v - qp.uA[i]) < 1e-5:
+            act.append(qp.A[i])
+    for j in range(qp.n):
+        if abs(x[j] - qp.lx[j]) < 1e-5 or abs(x[j] - qp.ux[j]) < 1e-5:
+            e = np.zeros(qp.n)
+            e[j] = 1
+            act.append(e)
+    G = np.array(act).reshape(len(act), qp.n)
+    N = sla.null_space(G) if len(act) else np.eye(qp.n)
+    g = np.random.default_rng(3).standard_normal(qp.n)
+    ref = -N @ np.linalg.solve(N.T @ H @ N, N.T @ g)
+    adj = oracle.adjoint_solve(res.scaled, res.state, res.mu, g)
+    assert np.max(np.abs(adj["p"] - ref)) <= 1e-4 * (1 + np.max(np.abs(ref)))
+
+
+def test_adjoint_finite_differences():
+    """dL/dp, dL/dlA, dL/duA against central differences of the IPM output."""
+    qp = qpgen.tiny_qp(6, 3, 5, me=0)
+    res = oracle.ipm_solve(qp)
+    rng = np.random.default_rng(9)
+    g = rng.standard_normal(qp.n)
+    adj = oracle.adjoint_solve(res.scaled, res.state, res.mu, g)
+    for _ in range(3):
+        dp = rng.standard_normal(qp.n)
+        dl = rng.standard_normal(qp.m)
+        du = rng.standard_normal(qp.m)
+        h = 1e-4
+        vals = []
+        for sgn in (1, -1):
+            q2 = qpgen.tiny_qp(6, 3, 5, me=0)
+            q2.p = qp.p + sgn * h * dp
+            q2.lA = qp.lA + sgn * h * dl
+            q2.uA = qp.uA + sgn * h * du
+            vals.append(g @ oracle.ipm_solve(q2).x)
+        fd = (vals[0] - vals[1]) / (2 * h)
+        an = adj["p"] @ dp + adj["lA"] @ dl + adj["uA"] @ du
+        assert abs(fd - an) <= 2e-3 * (1 + abs(an))
+
+
+# ---------------------------------------------------------------- settings
+def test_paper_settings_golden():
+    gold = json.load(open(os.path.join(GOLD, "paper_settings.json")))
+    import inspect
+    sig = inspect.signature(oracle.ipm_solve)
+    assert sig.parameters["gamma"].default == gold["gamma"]["value"]
+    assert sig.parameters["mu_tol"].default == gold["mu_tol"]["value"]
+    assert sig.parameters["pcg_tol"].default == gold["pcg_tol"]["value"]
+    assert sig.parameters["pcg_maxit"].default == gold["pcg_maxit"]["value"]
+    # Table 2 rows: parts add up to the total within the printed rounding
+    for row in gold["profiling_seconds"]["rows"]:
+        assert abs(sum(row[2:]) - row[1]) <= 0.01 * row[1] + 0.01
+
+
+def test_config0_converges_and_mu_rule():
+    """Config-0 run: converges, mu ends at 1e-7 (mu_tol 1e-6, strict test),
+    PCG-mode oracle reaches the same objective, and CG iterations grow as mu
+    decreases (section 5.1)."""
+    qp = qpgen.config0()
+    res = oracle.ipm_solve(qp, log=True)
+    assert res.status == "converged" and res.mu == pytest.approx(1e-7)
+    lA, uA, lx, ux, le = full_multipliers(res.scaled, res.lam, qp)
+    assert oracle.kkt_metrics(qp, res.x, lA, uA, lx, ux, le)["kkt_rel"] <= 1e-6
+    res2 = oracle.ipm_solve(qp, solver="pcg", log=True)
+    assert res2.status == "converged"
+    assert abs(qp.objective(res.x) - qp.objective(res2.x)) <= 1e-6 * (1 + abs(qp.objective(res.x)))
+    its = [h["pcg_iters"] for h in res2.log]
+    assert np.mean(its[-4:]) > 5 * np.mean(its[:4])
+
+
+def test_metrics_flag_bad_solution():
+    qp = qpgen.config0()
+    res = oracle.ipm_solve(qp)
+    lA, uA, lx, ux, le = full_multipliers(res.scaled, res.lam, qp)
+    good = oracle.kkt_metrics(qp, res.x, lA, uA, lx, ux, le)
+    bad = oracle.kkt_metrics(qp, res.x + 1e-3, lA, uA, lx, ux, le)
+    assert good["kkt_rel"] <= 1e-6 < bad["kkt_rel"]
