@@ -1,0 +1,225 @@
+/*
+ * kktqp.h - C ABI of the GB300 Krylov interior point library.
+ *
+ * Solves convex quadratic programs
+ *
+ *     min 1/2 x'Hx + p'x   s.t.  lA <= A x <= uA,  C x = b,  lx <= x <= ux     (Eq. (1))
+ *
+ * with the primal-dual interior point method of Liu, Fredriksson & Markidis
+ * (arXiv 2308.00637): each Newton step solves the doubly augmented KKT system
+ * (Eq. (9)) with Jacobi-preconditioned conjugate gradients, applied matrix-free
+ * from H, A, A' and the diagonal D built from slacks and multipliers (section
+ * 3.2); step lengths by the ratio test (Eq. (10)); mu divided by 10 whenever
+ * the residual norm drops below mu (Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *  - Pointers may be host or device memory (CUDA unified addressing decides);
+ *    the library copies inputs at qp_create and the caller keeps ownership of
+ *    every buffer it passes.  All device memory is owned by the handle and is
+ *    released by qp_destroy.
+ *  - Absent bounds are +-INFINITY.
+ *  - All work is ordered on the stream given at qp_create (NULL = legacy
+ *    default stream).  A handle is used by one host thread at a time.
+ *  - Every call returns a kq_status; none throws across the ABI.  After a
+ *    non-OK status qp_last_error(h) returns a message.
+ *  - Multiplier layout ("padded"): the KKT unknown of Eq. (9) is stored as
+ *        [ x (n) | lam_e (me) | lam_lA (m) | lam_uA (m) ]      NKP = n + me + 2m
+ *    where entries of lam_lA / lam_uA for rows whose bound is infinite are
+ *    identically zero (those rows are decoupled identity rows in K).
+ *  - Units: solutions (x, multipliers, slacks) returned by ipm_solve are in
+ *    the caller's original units.  kkt_apply / kkt_pcg_solve work on the
+ *    internally scaled system (objective scaled by sigma = 1/max(1, max H_ii,
+ *    |p|_inf), each A/C row and its bounds by 1/||row||_2).
+ */
+#ifndef KKTQP_H
+#define KKTQP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct kq_problem *kq_handle;
+typedef int kq_status;
+
+enum {
+  KQ_OK = 0,
+  KQ_ERR_ARG = 1,          /* invalid argument / unsupported combination      */
+  KQ_ERR_CUDA = 2,         /* a CUDA runtime call failed                       */
+  KQ_ERR_OOM = 3,          /* device allocation failed                         */
+  KQ_ERR_NOT_CONVEX = 4,   /* PCG met p'Kp <= 0: K not SPD (H not convex)      */
+  KQ_WARN_PCG_MAXIT = 5,   /* PCG stopped at its iteration cap; step was taken */
+  KQ_ERR_IPM_MAXIT = 6,    /* IPM iteration cap reached; best iterate returned */
+  KQ_ERR_TIMEOUT = 7,      /* a device-side grid barrier exceeded its budget   */
+  KQ_ERR_NUMERIC = 8,      /* NaN/Inf met in data or iterates                  */
+  KQ_ERR_STATE = 9         /* call order violated (e.g. backward before solve) */
+};
+
+/* H operator kinds (section 2.2 / section 3.2: H used only through products) */
+enum { KQ_H_DENSE = 0,     /* explicit symmetric n x n, row-major              */
+       KQ_H_CSR_LSQ = 1,   /* H = 2 P' diag(w) P, P CSR (rows x n)             */
+       KQ_H_LOWRANK = 2 }; /* H = Z Z', Z dense n x k row-major                */
+/* constraint-matrix kinds */
+enum { KQ_A_NONE = 0, KQ_A_DENSE = 1, KQ_A_ROWS_OF_P = 3 };
+/* storage types */
+enum { KQ_F64 = 0, KQ_F32 = 1, KQ_BF16 = 2 };
+/* arithmetic of the K products inside PCG */
+enum { KQ_PREC_F64 = 0,    /* all FP64                                          */
+       KQ_PREC_MIXED = 1 };/* FP32 matvec + FP32 accumulation; FP64 dots,
+                              diagonal, step and FP64 residual refinement       */
+
+typedef struct {
+  int kind;                /* KQ_H_*                                            */
+  int dtype;               /* storage of val/Z/H: KQ_F64, KQ_F32 or KQ_BF16     */
+  int64_t rows;            /* CSR_LSQ: rows of P;  LOWRANK: n;  DENSE: n       */
+  int64_t cols;            /* CSR_LSQ: n;          LOWRANK: k;  DENSE: n       */
+  int64_t nnz;             /* CSR_LSQ: nonzeros of P                            */
+  const void *val;         /* DENSE: H; LOWRANK: Z; CSR_LSQ: P values           */
+  const int32_t *col;      /* CSR_LSQ column indices (sorted not required)     */
+  const int64_t *rowptr;   /* CSR_LSQ row pointers (rows+1)                    */
+  const double *w;         /* CSR_LSQ row weights (rows), H = 2 P'diag(w)P     */
+} kq_hop;
+
+typedef struct {
+  int kind;                /* KQ_A_*                                            */
+  int dtype;               /* DENSE: KQ_F64 or KQ_F32                           */
+  int64_t m;               /* number of rows                                    */
+  const void *val;         /* DENSE: m x n row-major                            */
+  const int32_t *rows;     /* ROWS_OF_P: row ids into P (m), strictly increasing*/
+} kq_amat;
+
+typedef struct {
+  double gamma;            /* ratio-test factor, Eq. (10); paper: 0.99          */
+  double mu0;              /* initial mu (1.0)                                  */
+  double mu_tol;           /* return when ||r|| < mu and mu < mu_tol (1e-6)     */
+  int ipm_maxit;           /* Algorithm 1's N (200)                             */
+  double pcg_tol;          /* relative unpreconditioned residual (1e-7)         */
+  int pcg_maxit;           /* PCG iterations per Newton solve (5000)            */
+  int precision;           /* KQ_PREC_*                                         */
+  int refine_steps;        /* MIXED: FP32 correction solves before FP64 rescue  */
+  double inner_tol;        /* MIXED: relative tolerance of each FP32 solve      */
+  double timeout_s;        /* device barrier budget per wait (seconds)         */
+  int grid_ctas;           /* 0 = auto; else persistent-kernel grid size        */
+} kq_ipm_opts;
+
+typedef struct {
+  int status;              /* final kq_status                                   */
+  int ipm_iters;
+  double mu_final;
+  double res_norm;         /* ||r||_2 of Eq. (7)'s right-hand side, scaled units*/
+  double primal_inf, dual_inf, compl_inf;   /* section 5.2 norms, scaled units  */
+  long long pcg_iters;     /* total PCG iterations over the solve               */
+  int pcg_maxit_hits;      /* Newton solves that stopped at pcg_maxit           */
+  double time_s;           /* wall time of ipm_solve                            */
+  double pcg_time_s;       /* device time inside PCG solves (CUDA events)       */
+  double pcg_kernel_ms;    /* device time of the persistent PCG kernels only    */
+  long long pcg_launches;  /* persistent PCG kernel launches                    */
+} kq_ipm_stats;
+
+typedef struct {
+  double tol;              /* relative unpreconditioned residual                */
+  int maxit;
+  int precision;           /* KQ_PREC_*                                         */
+  int refine_steps;
+  double inner_tol;
+} kq_pcg_opts;
+
+typedef struct {
+  int status;
+  int iters;               /* PCG iterations over all passes                    */
+  int passes;              /* correction solves (1 unless refinement ran)       */
+  double rel_res;          /* true ||rhs - K z|| / ||rhs|| in FP64              */
+  double kernel_ms;        /* device time of the persistent kernels             */
+} kq_pcg_stats;
+
+/* Fill *o with the paper's settings (gamma 0.99, mu/10, mu_tol 1e-6, PCG tol
+ * 1e-7, 5000 PCG iterations; section 3.2 and section 5.1) and FP64. */
+void kq_default_ipm_opts(kq_ipm_opts *o);
+void kq_default_pcg_opts(kq_pcg_opts *o);
+
+/* qp_create: problem statement of Eq. (1) with bounds separated (section 3.1).
+ *  n      variables;  H  operator (required);  p  linear term (n)
+ *  A      general rows (may be NULL = none) with lA, uA (m each, +-inf = absent)
+ *  me     equality rows; C dense me x n row-major FP64 and b (me); NULL if me=0
+ *  lx,ux  variable bounds (n each, may be NULL = free)
+ *  stream cudaStream_t (as void*), NULL for the default stream
+ * Supported: DENSE H (F64/F32/BF16) with A NONE or DENSE (F64/F32) and any me;
+ * CSR_LSQ H (F32 values) with A NONE or ROWS_OF_P and me = 0; LOWRANK H
+ * (F32/F64) with A NONE and any me.  Errors: KQ_ERR_ARG for bad sizes or an
+ * unsupported combination, KQ_ERR_OOM, KQ_ERR_CUDA.  *out is NULL on error. */
+kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
+                    const kq_amat *A, const double *lA, const double *uA,
+                    int64_t me, const double *C, const double *b,
+                    const double *lx, const double *ux, void *stream);
+
+/* ipm_solve: Algorithm 1 from the initial point (or from the state set by
+ * qp_set_state).  Outputs (any may be NULL), original units:
+ *  x (n); lam_lA, lam_uA (m, zero where the bound is absent); lam_lx, lam_ux
+ *  (n); lam_e (me).  Returns KQ_OK on convergence, KQ_ERR_IPM_MAXIT (outputs
+ *  hold the last iterate), or an error. */
+kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x,
+                    double *lam_lA, double *lam_uA, double *lam_lx,
+                    double *lam_ux, double *lam_e, kq_ipm_stats *stats);
+
+/* kkt_pcg_solve: Jacobi-PCG on the K of Eq. (9) at the current iterate and
+ * barrier parameter, scaled units, padded layout (NKP = n + me + 2m).
+ * rhs, sol: NKP doubles.  z0 = 0. */
+kq_status kkt_pcg_solve(kq_handle h, const double *rhs, double *sol,
+                        const kq_pcg_opts *opts, kq_pcg_stats *stats);
+
+/* kkt_apply: out = K v (Eq. (9)) at the current iterate, FP64 or MIXED
+ * arithmetic, scaled units, padded layout. */
+kq_status kkt_apply(kq_handle h, const double *v, double *out, int precision);
+
+/* kkt_diag: Jacobi diagonal diag(K) at the current iterate (NKP). */
+kq_status kkt_diag(kq_handle h, double *diag);
+
+/* qp_backward: after a converged ipm_solve, gradients of L = gbar'x* with
+ * respect to p, lA, uA and b by one extra PCG solve with the converged K
+ * (K [v; w] = [gbar; 0]).  Original units; outputs may be NULL.  Rows or
+ * entries whose bound is infinite get 0.  KQ_ERR_STATE if no solve ran. */
+kq_status qp_backward(kq_handle h, const double *gbar, double *grad_p,
+                      double *grad_lA, double *grad_uA, double *grad_b,
+                      const kq_pcg_opts *opts, kq_pcg_stats *stats);
+
+/* Iterate access (checkpoint / warm start / testing), scaled units.
+ * x (n); s_lA, s_uA, lam_lA, lam_uA (m); s_lx, s_ux, lam_lx, lam_ux (n);
+ * lam_e (me); *mu.  Entries for absent bounds are ignored on set and returned
+ * as s = 1, lam = 0 on get. */
+kq_status qp_get_state(kq_handle h, double *x, double *s_lA, double *s_uA,
+                       double *s_lx, double *s_ux, double *lam_lA,
+                       double *lam_uA, double *lam_lx, double *lam_ux,
+                       double *lam_e, double *mu);
+kq_status qp_set_state(kq_handle h, const double *x, const double *s_lA,
+                       const double *s_uA, const double *s_lx,
+                       const double *s_ux, const double *lam_lA,
+                       const double *lam_uA, const double *lam_lx,
+                       const double *lam_ux, const double *lam_e, double mu);
+
+/* qp_residuals: residual blocks of Eq. (7) at the current iterate and mu
+ * (scaled units): r_H (n), r_lA, r_uA, r_c1, r_c2 (m), r_lx, r_ux, r_c3,
+ * r_c4 (n), r_e (me), plus the doubly augmented right-hand side of Eq. (9)
+ * rhs (NKP) and *norm = ||r||_2.  Any pointer may be NULL. */
+kq_status qp_residuals(kq_handle h, double *r_H, double *r_lA, double *r_uA,
+                       double *r_c1, double *r_c2, double *r_lx, double *r_ux,
+                       double *r_c3, double *r_c4, double *r_e, double *rhs,
+                       double *norm);
+
+/* Scale factors chosen at create: *sigma, rhoA (m), rhoC (me). */
+kq_status qp_scaling(kq_handle h, double *sigma, double *rhoA, double *rhoC);
+
+/* Sizes: n, m, me, NKP. */
+kq_status qp_sizes(kq_handle h, int64_t *n, int64_t *m, int64_t *me, int64_t *nkp);
+
+const char *qp_last_error(kq_handle h);
+void qp_destroy(kq_handle h);
+
+/* Library-wide: message of the last failure of a call that had no handle
+ * (qp_create). */
+const char *kq_global_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* KKTQP_H */

@@ -1,0 +1,132 @@
+// Internal structures of the Krylov IPM library (host + device views).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+#include "../../include/kktqp.h"
+
+// Device view of a scaled problem (all pointers are device memory).
+struct DevProb {
+  int64_t n = 0, m = 0, me = 0, nkp = 0;
+  int hkind = 0, hdtype = 0;
+  double hscale = 1.0;               // sigma (DENSE, LOWRANK): H_scaled = hscale * H
+  // DENSE H (scaled by sigma), n x n row-major
+  const void *Hd = nullptr;
+  // CSR_LSQ: H = P' diag(w2) P, w2 = 2 sigma w
+  int64_t nP = 0, nnz = 0;
+  const int64_t *rowptr = nullptr;
+  const int32_t *col = nullptr;
+  const float *val = nullptr;
+  const double *w2 = nullptr;
+  const int32_t *prow2a = nullptr;   // nP: A-row id or -1
+  const int32_t *arows = nullptr;    // m: P row of A row
+  // LOWRANK: H = Zs Zs', Zs = sqrt(sigma) Z, n x k row-major
+  int64_t k = 0;
+  const void *Z = nullptr;
+  // dense A (rows already scaled), m x n row-major
+  int akind = 0, adtype = 0;
+  const void *Ad = nullptr;
+  const double *rhoA = nullptr;      // m (ROWS_OF_P: applied on the fly)
+  const double *lA = nullptr, *uA = nullptr;   // scaled, m
+  const uint8_t *hasl = nullptr, *hasu = nullptr;
+  // equality rows (scaled), me x n row-major, and rhs
+  const double *Cd = nullptr, *b = nullptr;
+  const double *p = nullptr;         // scaled linear term
+  const double *lx = nullptr, *ux = nullptr;
+  const uint8_t *haslx = nullptr, *hasux = nullptr;
+  const double *hdiag = nullptr;     // diag(H) scaled (zeros for CSR_LSQ: added in pass)
+};
+
+// Device state of the iterate (scaled units).
+struct DevState {
+  double *x, *slx, *sux, *llx, *lux;  // n
+  double *sl, *su, *ll, *lu;          // m
+  double *le;                         // me
+};
+
+// Per-iterate KKT data produced by the residual pass.
+struct DevKKT {
+  double *Dl, *Du, *cl, *cu;   // m: D blocks and masked inverses
+  double *dg;                  // n
+  double *diag;                // nkp Jacobi diagonal
+  double *rhs;                 // nkp doubly augmented rhs
+  double *rH, *rlx, *rux, *rc3, *rc4;   // n
+  double *rlA, *ruA, *rc1, *rc2;        // m
+  double *re;                           // me
+  double mu;
+};
+
+// Work space of the persistent PCG kernels.
+struct PcgWork {
+  int G = 0;                   // CTAs of the cooperative launch
+  int threads = 0;
+  int win_cap = 0;             // smem window capacity (elements)
+  size_t smem = 0;             // dynamic smem bytes
+  double *r = nullptr, *y = nullptr, *pb0 = nullptr, *pb1 = nullptr;
+  double *qlam = nullptr;      // me + 2m
+  double *accx64 = nullptr;    // n
+  float *accx32 = nullptr;     // n
+  double *g64 = nullptr;       // k + me (LOWRANK)
+  double *slots = nullptr;     // 4 * G
+  unsigned int *bar = nullptr; // [count, gen]
+  int *err = nullptr;          // device error flag
+  int *iters = nullptr;        // device iteration count
+  double *resn = nullptr;      // device final recursive residual^2, bb
+  int64_t *row_begin = nullptr;   // G+1 partition of rows (P rows / dense rows)
+  int32_t *win_lo = nullptr, *win_hi = nullptr;  // G column windows (CSR)
+  int *h_pinned = nullptr;     // pinned host mirror for status words
+};
+
+struct kq_problem {
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int64_t n = 0, m = 0, me = 0, nkp = 0;
+  double sigma = 1.0;
+  DevProb P;
+  DevState S;
+  DevKKT K;
+  PcgWork W;
+  std::vector<void *> allocs;   // every device allocation, freed at destroy
+  // scratch for IPM kernels
+  double *hx = nullptr, *t = nullptr, *tC = nullptr, *acc1 = nullptr, *acc2 = nullptr,
+         *acc3 = nullptr, *yP = nullptr, *g = nullptr;
+  double *z = nullptr, *zref = nullptr, *tmp = nullptr;
+  double *dsl = nullptr, *dsu = nullptr, *dslx = nullptr, *dsux = nullptr, *dllx = nullptr,
+         *dlux = nullptr;
+  double *red = nullptr;        // reduction partials
+  double *red_out = nullptr;    // reduction results (device)
+  double *h_red = nullptr;      // pinned host mirror of results
+  double *rhoC = nullptr;       // equality row scales (me)
+  int *dflags = nullptr;        // reduction kind flags (8)
+  bool state_set = false;       // qp_set_state supplied the starting iterate
+  double mu = 1.0;
+  int mu_exp = 0;
+  bool kkt_valid = false;       // K data matches the current state and mu
+  bool solved = false;          // a converged ipm_solve ran
+  int num_sms = 0;
+  double timeout_s = 2.0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+// ---------------------------------------------------------------- host helpers
+kq_status kq_fail(kq_problem *h, kq_status st, const std::string &msg);
+#define KQ_CUDA(h, call)                                                       \
+  do {                                                                         \
+    cudaError_t e_ = (call);                                                   \
+    if (e_ != cudaSuccess)                                                     \
+      return kq_fail((h), KQ_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// pcg.cu
+kq_status pcg_setup(kq_problem *h, int grid_ctas);
+// Solve K z = rhs (device pointers, padded layout) with Jacobi PCG.
+kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_opts &o,
+                    kq_pcg_stats *st);
+// out = K v in FP64 (prec = KQ_PREC_F64) or mixed arithmetic.
+kq_status pcg_apply(kq_problem *h, const double *v, double *out, int prec, float *ms);
+double pcg_last_kernel_ms();
+
+// ipm kernels (ipm.cu)
+kq_status kkt_assemble(kq_problem *h);   // residuals, rhs, D, diag at state & mu

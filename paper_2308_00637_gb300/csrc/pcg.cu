@@ -1,0 +1,770 @@
+// Persistent Jacobi-PCG on the doubly augmented KKT system (Eq. (9)).
+//
+//   K = [ Q + 2 B'D^-1 B   B' ]      Q = H + diag(dg),  B = [C; A_L; -A_U]
+//       [ B                D  ]      D = diag(mu 1, S_lA/Lam_lA, S_uA/Lam_uA)
+//
+// K is never formed (section 3.2): one product K p is a single pass over the
+// rows of the operator.  For a general row i with t_i = A_i p_x,
+//     top    += A_i' (2 t_i (1/D_li + 1/D_ui) + p_li - p_ui)
+//     bottom  = ( t_i + D_li p_li,  -t_i + D_ui p_ui )
+// so A is read once per product (two-sided rows folded).  For the dose
+// structure (H = 2 P'WP, A = scaled rows of P) the H and A parts share the
+// same read of P.
+//
+// One cooperative launch runs the whole PCG solve.  Per iteration:
+//   phase A  : q = K p, with p = y + beta p_old formed on the fly (so the
+//              search direction update needs no barrier of its own), and the
+//              partial sums of p'q (p'Aq terms by linearity: p_x'A' c = c't);
+//   barrier  : alpha = rho / p'q;
+//   phase C  : z += alpha p, r -= alpha q, y = r / diag(K), partial |r|^2, r'y;
+//   barrier  : beta = rho'/rho, convergence test |r| <= tol |rhs|.
+// Dots are FP64 and summed in a fixed order (deterministic).  Every barrier
+// wait is bounded; on expiry the kernel records a status and returns.
+#include "common.cuh"
+#include "kq_internal.h"
+#include <algorithm>
+#include <vector>
+
+namespace {
+
+struct PcgArgs {
+  DevProb P;
+  const double *Dl, *Du, *cl, *cu, *dg, *diag;
+  double mu;
+  const double *rhs;   // right-hand side (SOLVE) or the vector v (APPLY)
+  double *z;           // solution (SOLVE) or K v (APPLY)
+  double *r, *y, *pb0, *pb1, *qlam;
+  void *accx;
+  double *g;
+  double *slots;
+  const int64_t *row_begin;
+  const int32_t *win_lo, *win_hi;
+  int win_cap;
+  GridBar bar;
+  double tol2;
+  int maxit;
+  int apply;
+  int *iters;
+  double *resn;
+};
+
+__device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
+
+
+// Sum of G slot values in a fixed order (identical in every CTA).
+__device__ __forceinline__ double sum_slots(const double *s, int G, double *sh) {
+  double v = 0.0;
+  if (threadIdx.x < 32) {
+    for (int i = threadIdx.x; i < G; i += 32) v += __ldcg(s + i);
+    v = warp_sum(v);
+    if (threadIdx.x == 0) sh[0] = v;
+  }
+  __syncthreads();
+  v = sh[0];
+  __syncthreads();
+  return v;
+}
+
+// p_new for this CTA's owned vector entries; returns sum dg_j p_j^2 (x part)
+__device__ __forceinline__ double write_owned_p(const PcgArgs &a, const double *ysrc,
+                                                const double *pold, double *pnew, double beta,
+                                                int64_t vb, int64_t ve) {
+  double pq = 0.0;
+  const int64_t n = a.P.n;
+  for (int64_t i = vb + threadIdx.x; i < ve; i += blockDim.x) {
+    double pi = ldcg(ysrc + i) + beta * ldcg(pold + i);
+    pnew[i] = pi;
+    if (i < n) pq += a.dg[i] * pi * pi;
+  }
+  return pq;
+}
+
+// ---------------------------------------------------------------- CSR (H = P'W2P, A = rows of P)
+struct OpCsr {
+  template <class T>
+  static __device__ double phaseA(const PcgArgs &a, const double *ysrc, const double *pold,
+                                  double *pnew, double beta, int64_t vb, int64_t ve,
+                                  unsigned char *smem) {
+    const DevProb &P = a.P;
+    const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    const int lo = a.win_lo[cta], hi = a.win_hi[cta];
+    const int wlen = hi - lo;
+    const bool win = wlen <= a.win_cap;
+    T *pw = reinterpret_cast<T *>(smem);
+    T *acc = pw + a.win_cap;
+    T *accg = reinterpret_cast<T *>(a.accx);
+    double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
+    if (win) {
+      for (int j = tid; j < wlen; j += blockDim.x) {
+        const int c = lo + j;
+        pw[j] = (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+        acc[j] = (T)0;
+      }
+    }
+    __syncthreads();
+    const int64_t r0 = a.row_begin[cta], r1 = a.row_begin[cta + 1];
+    const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
+    for (int64_t r = r0 + warp; r < r1; r += nw) {
+      const int64_t s = P.rowptr[r], e = P.rowptr[r + 1];
+      T dot = (T)0;
+      const bool short_row = (e - s) <= 128;
+      float vv[4];
+      int cc[4];
+      if (short_row) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int64_t kk = s + lane + 32 * q;
+          if (kk < e) {
+            vv[q] = ld_stream(P.val + kk);
+            cc[q] = ld_stream(P.col + kk);
+          } else {
+            vv[q] = 0.f;
+            cc[q] = -1;
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (cc[q] >= 0) {
+            T pv = win ? pw[cc[q] - lo]
+                       : (T)(ldcg(ysrc + cc[q]) + beta * ldcg(pold + cc[q]));
+            dot += (T)vv[q] * pv;
+          }
+        }
+      } else {
+        for (int64_t kk = s + lane; kk < e; kk += 32) {
+          const int c = P.col[kk];
+          T pv = win ? pw[c - lo] : (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+          dot += (T)P.val[kk] * pv;
+        }
+      }
+      dot = warp_sum(dot);
+      const double dd = (double)dot;
+      double ud = P.w2[r] * dd;
+      const int ai = P.prow2a[r];
+      if (ai >= 0) {
+        const double rho_a = P.rhoA[ai];
+        const double t = rho_a * dd;
+        const bool hl = P.hasl[ai] != 0, hu = P.hasu[ai] != 0;
+        const double pl = hl ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
+        const double pu = hu ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
+        const double coef = 2.0 * t * (a.cl[ai] + a.cu[ai]) + pl - pu;
+        ud += rho_a * coef;
+        if (lane == 0) {
+          const double ql = hl ? t + a.Dl[ai] * pl : 0.0;
+          const double qu = hu ? -t + a.Du[ai] * pu : 0.0;
+          a.qlam[P.me + ai] = ql;
+          a.qlam[P.me + P.m + ai] = qu;
+          pq += pl * ql + pu * qu;
+        }
+      }
+      if (lane == 0) pq += ud * dd;
+      const T u = (T)ud;
+      if (short_row) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (cc[q] >= 0) {
+            if (win) atomicAdd(acc + (cc[q] - lo), u * (T)vv[q]);
+            else atomicAdd(accg + cc[q], u * (T)vv[q]);
+          }
+        }
+      } else {
+        for (int64_t kk = s + lane; kk < e; kk += 32) {
+          const int c = P.col[kk];
+          if (win) atomicAdd(acc + (c - lo), u * (T)P.val[kk]);
+          else atomicAdd(accg + c, u * (T)P.val[kk]);
+        }
+      }
+    }
+    __syncthreads();
+    if (win) {
+      for (int j = tid; j < wlen; j += blockDim.x) {
+        const T v = acc[j];
+        if (v != (T)0) atomicAdd(accg + lo + j, v);
+      }
+    }
+    return pq;
+  }
+};
+
+// ---------------------------------------------------------------- DENSE (explicit H, dense A, C)
+template <class HS, class AS>
+struct OpDense {
+  template <class T>
+  static __device__ double phaseA(const PcgArgs &a, const double *ysrc, const double *pold,
+                                  double *pnew, double beta, int64_t vb, int64_t ve,
+                                  unsigned char *smem) {
+    const DevProb &P = a.P;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    const int64_t n = P.n, m = P.m, me = P.me;
+    T *pw = reinterpret_cast<T *>(smem);
+    T *acc = pw + a.win_cap;
+    T *accg = reinterpret_cast<T *>(a.accx);
+    double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
+    for (int64_t j = tid; j < n; j += blockDim.x) {
+      pw[j] = (T)(ldcg(ysrc + j) + beta * ldcg(pold + j));
+      acc[j] = (T)0;
+    }
+    __syncthreads();
+    const HS *Hd = reinterpret_cast<const HS *>(P.Hd);
+    const AS *Ad = reinterpret_cast<const AS *>(P.Ad);
+    const int64_t R = n + m + me;
+    const int64_t gw0 = (int64_t)blockIdx.x * nw + warp, GW = (int64_t)gridDim.x * nw;
+    const int64_t lo_off = n + me, up_off = n + me + m;
+    for (int64_t row = gw0; row < R; row += GW) {
+      if (row < n) {
+        const HS *h = Hd + row * n;
+        T dot = (T)0;
+        for (int64_t j = lane; j < n; j += 32) dot += (T)ld_as_f64(h, j) * pw[j];
+        dot = warp_sum(dot) * (T)P.hscale;
+        if (lane == 0) {
+          atomicAdd(acc + row, dot);
+          const double prow = ldcg(ysrc + row) + beta * ldcg(pold + row);
+          pq += prow * (double)dot;
+        }
+      } else if (row < n + m) {
+        const int64_t ai = row - n;
+        const bool hl = P.hasl[ai] != 0, hu = P.hasu[ai] != 0;
+        if (!hl && !hu) {
+          if (lane == 0) { a.qlam[me + ai] = 0.0; a.qlam[me + m + ai] = 0.0; }
+          continue;
+        }
+        const AS *ar = Ad + ai * n;
+        T dot = (T)0;
+        for (int64_t j = lane; j < n; j += 32) dot += (T)ld_as_f64(ar, j) * pw[j];
+        dot = warp_sum(dot);
+        const double rho_a = P.rhoA[ai];
+        const double t = rho_a * (double)dot;
+        const double pl = hl ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
+        const double pu = hu ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
+        const double coef = 2.0 * t * (a.cl[ai] + a.cu[ai]) + pl - pu;
+        const T cf = (T)(coef * rho_a);
+        for (int64_t j = lane; j < n; j += 32) atomicAdd(acc + j, cf * (T)ld_as_f64(ar, j));
+        if (lane == 0) {
+          const double ql = hl ? t + a.Dl[ai] * pl : 0.0;
+          const double qu = hu ? -t + a.Du[ai] * pu : 0.0;
+          a.qlam[me + ai] = ql;
+          a.qlam[me + m + ai] = qu;
+          pq += coef * t + pl * ql + pu * qu;
+        }
+      } else {
+        const int64_t e = row - n - m;
+        const double *cr = P.Cd + e * n;
+        T dot = (T)0;
+        for (int64_t j = lane; j < n; j += 32) dot += (T)cr[j] * pw[j];
+        dot = warp_sum(dot);
+        const double t = (double)dot;
+        const double pe = ldcg(ysrc + n + e) + beta * ldcg(pold + n + e);
+        const double coef = 2.0 * t / a.mu + pe;
+        const T cf = (T)coef;
+        for (int64_t j = lane; j < n; j += 32) atomicAdd(acc + j, cf * (T)cr[j]);
+        if (lane == 0) {
+          const double qe = t + a.mu * pe;
+          a.qlam[e] = qe;
+          pq += coef * t + pe * qe;
+        }
+      }
+    }
+    __syncthreads();
+    for (int64_t j = tid; j < n; j += blockDim.x) {
+      const T v = acc[j];
+      if (v != (T)0) atomicAdd(accg + j, v);
+    }
+    return pq;
+  }
+};
+
+// ---------------------------------------------------------------- LOWRANK (H = Z Z', equality rows C)
+template <class ZS>
+struct OpLowrank {
+  template <class T>
+  static __device__ double phaseA(const PcgArgs &a, const double *ysrc, const double *pold,
+                                  double *pnew, double beta, int64_t vb, int64_t ve,
+                                  unsigned char *smem, bool &ok) {
+    const DevProb &P = a.P;
+    const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    const int64_t n = P.n, k = P.k, me = P.me, kk = k + me;
+    const ZS *Z = reinterpret_cast<const ZS *>(P.Z);
+    T *accg = reinterpret_cast<T *>(a.accx);
+    double *ps = reinterpret_cast<double *>(smem);          // p for this CTA's rows
+    double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
+    const int64_t r0 = a.row_begin[cta], r1 = a.row_begin[cta + 1];
+    for (int64_t i = r0 + tid; i < r1; i += blockDim.x)
+      ps[i - r0] = ldcg(ysrc + i) + beta * ldcg(pold + i);
+    __syncthreads();
+    // phase A1: g = [Z C']' p_x  (partial over this CTA's rows)
+    for (int64_t c = tid; c < kk; c += blockDim.x) {
+      T s = (T)0;
+      if (c < k) {
+        for (int64_t i = r0; i < r1; ++i) s += (T)ld_as_f64(Z, i * k + c) * (T)ps[i - r0];
+      } else {
+        const double *cr = P.Cd + (c - k) * n;
+        for (int64_t i = r0; i < r1; ++i) s += (T)cr[i] * (T)ps[i - r0];
+      }
+      atomicAdd(a.g + c, (double)s);
+    }
+    ok = grid_sync(a.bar);
+    if (!ok) return 0.0;
+    // phase A2: (Z g)_i + sum_e C_ei (2 t_e / mu + p_e)
+    double *cf = ps + a.win_cap;                          // me coefficients
+    T *gs = reinterpret_cast<T *>(cf + me + 1);           // g = [Z C']'p_x
+    for (int64_t c = tid; c < kk; c += blockDim.x) gs[c] = (T)(__ldcg(a.g + c) * (c < k ? P.hscale : 1.0));
+    for (int64_t e = tid; e < me; e += blockDim.x) {
+      const double t = __ldcg(a.g + k + e);
+      const double pe = ldcg(ysrc + n + e) + beta * ldcg(pold + n + e);
+      cf[e] = 2.0 * t / a.mu + pe;
+      if (cta == 0) {
+        const double qe = t + a.mu * pe;
+        a.qlam[e] = qe;
+        pq += pe * qe;
+      }
+    }
+    __syncthreads();
+    for (int64_t i = r0 + warp; i < r1; i += nw) {
+      T s = (T)0;
+      for (int64_t c = lane; c < k; c += 32) s += (T)ld_as_f64(Z, i * k + c) * gs[c];
+      s = warp_sum(s);
+      if (lane == 0) {
+        double hz = (double)s;
+        for (int64_t e = 0; e < me; ++e) hz += P.Cd[e * n + i] * cf[e];
+        accg[i] = (T)hz;
+        pq += ps[i - r0] * hz;
+      }
+    }
+    return pq;
+  }
+};
+
+template <class OP> struct IsLowrank { static constexpr bool value = false; };
+template <class ZS> struct IsLowrank<OpLowrank<ZS>> { static constexpr bool value = true; };
+
+template <class OP, class T>
+__device__ __forceinline__ double run_phaseA(const PcgArgs &a, const double *ysrc,
+                                             const double *pold, double *pnew, double beta,
+                                             int64_t vb, int64_t ve, unsigned char *smem,
+                                             bool &ok) {
+  if constexpr (IsLowrank<OP>::value) {
+    return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ok);
+  } else {
+    ok = true;
+    return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem);
+  }
+}
+
+template <class OP, class T>
+__global__ void __launch_bounds__(512, 1) pcg_kernel(PcgArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sh[32 * 2];
+  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+  const int64_t nkp = a.P.nkp, n = a.P.n;
+  const int64_t chunk = ceil_div64(nkp, G);
+  const int64_t vb = min(nkp, (int64_t)cta * chunk), ve = min(nkp, vb + chunk);
+  T *accg = reinterpret_cast<T *>(a.accx);
+  double *pold = a.pb0, *pnew = a.pb1;
+  double beta = 0.0, rho = 0.0, bb = 0.0, rr = 0.0;
+  int it = 0;
+  bool ok = true;
+  const double *ysrc = a.apply ? a.rhs : a.y;
+
+  // ---- initialisation: z = 0, r = rhs, y = r / diag, p_old = 0
+  {
+    double part[2] = {0.0, 0.0};
+    for (int64_t i = vb + tid; i < ve; i += blockDim.x) {
+      pold[i] = 0.0;
+      if (i < n) accg[i] = (T)0;
+      if (!a.apply) {
+        const double ri = a.rhs[i];
+        const double yi = ri / a.diag[i];
+        a.z[i] = 0.0;
+        a.r[i] = ri;
+        a.y[i] = yi;
+        part[0] += ri * ri;
+        part[1] += ri * yi;
+      }
+    }
+    if (cta == 0 && a.g)
+      for (int64_t c = tid; c < a.P.k + a.P.me; c += blockDim.x) a.g[c] = 0.0;
+    block_sum<2>(part, sh);
+    if (tid == 0) { a.slots[cta] = part[0]; a.slots[G + cta] = part[1]; }
+  }
+  ok = grid_sync(a.bar);
+  if (ok && !a.apply) {
+    bb = sum_slots(a.slots, G, sh);
+    rho = sum_slots(a.slots + G, G, sh);
+    rr = bb;
+  }
+  while (ok) {
+    if (!a.apply && (rr <= a.tol2 * bb || it >= a.maxit)) break;
+    // ---- phase A: q = K p,  p = y + beta p_old
+    double pq = run_phaseA<OP, T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ok);
+    if (!ok) break;
+    {
+      double v1[1] = {pq};
+      block_sum<1>(v1, sh);
+      if (tid == 0) a.slots[2 * G + cta] = v1[0];
+    }
+    ok = grid_sync(a.bar);
+    if (!ok) break;
+    if (a.apply) {
+      for (int64_t i = vb + tid; i < ve; i += blockDim.x) {
+        const double pi = pnew[i];
+        a.z[i] = (i < n) ? (double)__ldcg(accg + i) + a.dg[i] * pi : __ldcg(a.qlam + (i - n));
+      }
+      break;
+    }
+    const double pqt = sum_slots(a.slots + 2 * G, G, sh);
+    if (!(pqt > 0.0)) {
+      if (tid == 0 && cta == 0) atomicCAS(a.bar.err, 0, isnan(pqt) ? 8 : 4);
+      break;
+    }
+    const double alpha = rho / pqt;
+    // ---- phase C: vector updates on owned entries
+    double part[2] = {0.0, 0.0};
+    for (int64_t i = vb + tid; i < ve; i += blockDim.x) {
+      const double pi = pnew[i];
+      double qi;
+      if (i < n) {
+        qi = (double)__ldcg(accg + i) + a.dg[i] * pi;
+        accg[i] = (T)0;
+      } else {
+        qi = __ldcg(a.qlam + (i - n));
+      }
+      a.z[i] += alpha * pi;
+      const double ri = a.r[i] - alpha * qi;
+      a.r[i] = ri;
+      const double yi = ri / a.diag[i];
+      a.y[i] = yi;
+      part[0] += ri * ri;
+      part[1] += ri * yi;
+    }
+    if (cta == 0 && a.g)
+      for (int64_t c = tid; c < a.P.k + a.P.me; c += blockDim.x) a.g[c] = 0.0;
+    block_sum<2>(part, sh);
+    if (tid == 0) { a.slots[cta] = part[0]; a.slots[G + cta] = part[1]; }
+    ok = grid_sync(a.bar);
+    if (!ok) break;
+    rr = sum_slots(a.slots, G, sh);
+    const double rho_new = sum_slots(a.slots + G, G, sh);
+    beta = rho_new / rho;
+    rho = rho_new;
+    double *t = pold; pold = pnew; pnew = t;
+    ++it;
+  }
+  if (cta == 0 && tid == 0) {
+    *a.iters = it;
+    a.resn[0] = rr;
+    a.resn[1] = bb;
+  }
+}
+
+// column window [lo, hi) of each CTA's row range (CSR)
+__global__ void k_windows(const int64_t *rowptr, const int32_t *col, const int64_t *row_begin,
+                          int32_t *lo, int32_t *hi) {
+  __shared__ double sh[32];
+  const int c = blockIdx.x;
+  const int64_t s = rowptr[row_begin[c]], e = rowptr[row_begin[c + 1]];
+  double mn = INFINITY, mx = -INFINITY;
+  for (int64_t k = s + threadIdx.x; k < e; k += blockDim.x) {
+    const double v = (double)col[k];
+    mn = fmin(mn, v);
+    mx = fmax(mx, v);
+  }
+  mn = block_min(mn, sh);
+  mx = -block_min(-mx, sh);
+  if (threadIdx.x == 0) {
+    if (e > s) { lo[c] = (int32_t)mn; hi[c] = (int32_t)mx + 1; }
+    else { lo[c] = 0; hi[c] = 0; }
+  }
+}
+
+__global__ void k_axpy_res(int64_t N, const double *rhs, const double *kz, double *res,
+                           double *part) {
+  __shared__ double sh[32];
+  double s[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = rhs[i] - kz[i];
+    res[i] = v;
+    s[0] += v * v;
+  }
+  block_sum<1>(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void k_sumsq(int64_t N, const double *v, double *part) {
+  __shared__ double sh[32];
+  double s[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    s[0] += v[i] * v[i];
+  block_sum<1>(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+__global__ void k_add(int64_t N, double *z, const double *dz) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    z[i] += dz[i];
+}
+
+__global__ void k_final_sum(int nb, const double *part, double *out) {
+  __shared__ double sh[32];
+  double s[1] = {0.0};
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) s[0] += part[i];
+  block_sum<1>(s, sh);
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+using KFun = void (*)(PcgArgs);
+
+template <class T> KFun pick_kernel(const DevProb &P) {
+  if (P.hkind == KQ_H_CSR_LSQ) return pcg_kernel<OpCsr, T>;
+  if (P.hkind == KQ_H_LOWRANK) {
+    if (P.hdtype == KQ_F64) return pcg_kernel<OpLowrank<double>, T>;
+    return pcg_kernel<OpLowrank<float>, T>;
+  }
+  // DENSE
+  const bool a64 = P.adtype == KQ_F64;
+  if (P.hdtype == KQ_F64) return a64 ? pcg_kernel<OpDense<double, double>, T> : pcg_kernel<OpDense<double, float>, T>;
+  if (P.hdtype == KQ_F32) return a64 ? pcg_kernel<OpDense<float, double>, T> : pcg_kernel<OpDense<float, float>, T>;
+  return a64 ? pcg_kernel<OpDense<__nv_bfloat16, double>, T> : pcg_kernel<OpDense<__nv_bfloat16, float>, T>;
+}
+
+float g_last_ms = 0.f;
+
+template <class X> X *dalloc(kq_problem *h, size_t count) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(X)) != cudaSuccess) return nullptr;
+  h->allocs.push_back(p);
+  return reinterpret_cast<X *>(p);
+}
+
+kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double tol, int maxit,
+                 int apply, int *iters_out, double *rr_out, double *bb_out) {
+  PcgWork &W = h->W;
+  PcgArgs a;
+  a.P = h->P;
+  a.Dl = h->K.Dl; a.Du = h->K.Du; a.cl = h->K.cl; a.cu = h->K.cu;
+  a.dg = h->K.dg; a.diag = h->K.diag; a.mu = h->K.mu;
+  a.rhs = rhs; a.z = z;
+  a.r = W.r; a.y = W.y; a.pb0 = W.pb0; a.pb1 = W.pb1; a.qlam = W.qlam;
+  a.accx = prec == KQ_PREC_MIXED ? (void *)W.accx32 : (void *)W.accx64;
+  a.g = (h->P.hkind == KQ_H_LOWRANK) ? W.g64 : nullptr;
+  a.slots = W.slots;
+  a.row_begin = W.row_begin; a.win_lo = W.win_lo; a.win_hi = W.win_hi; a.win_cap = W.win_cap;
+  a.bar.count = W.bar; a.bar.gen = W.bar + 1; a.bar.err = W.err; a.bar.nblocks = W.G;
+  a.bar.budget_ns = (uint64_t)(h->timeout_s * 1e9);
+  a.tol2 = tol * tol; a.maxit = maxit; a.apply = apply;
+  a.iters = W.iters; a.resn = W.resn;
+  KFun f = prec == KQ_PREC_MIXED ? pick_kernel<float>(h->P) : pick_kernel<double>(h->P);
+  KQ_CUDA(h, cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)W.smem));
+  KQ_CUDA(h, cudaMemsetAsync(W.err, 0, sizeof(int), h->stream));
+  KQ_CUDA(h, cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), h->stream));
+  void *args[] = {&a};
+  KQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
+  KQ_CUDA(h, cudaLaunchCooperativeKernel((const void *)f, dim3(W.G), dim3(W.threads), args,
+                                         W.smem, h->stream));
+  KQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
+  // status words back to the host
+  KQ_CUDA(h, cudaMemcpyAsync(W.h_pinned, W.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  KQ_CUDA(h, cudaMemcpyAsync(W.h_pinned + 1, W.iters, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  KQ_CUDA(h, cudaMemcpyAsync(W.h_pinned + 2, W.resn, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  KQ_CUDA(h, cudaStreamSynchronize(h->stream));
+  KQ_CUDA(h, cudaEventElapsedTime(&g_last_ms, h->ev0, h->ev1));
+  const int err = W.h_pinned[0];
+  if (iters_out) *iters_out = W.h_pinned[1];
+  double rb[2];
+  memcpy(rb, W.h_pinned + 2, sizeof rb);
+  if (rr_out) *rr_out = rb[0];
+  if (bb_out) *bb_out = rb[1];
+  if (err == 7) return kq_fail(h, KQ_ERR_TIMEOUT, "PCG grid barrier exceeded its time budget");
+  if (err == 4) return kq_fail(h, KQ_ERR_NOT_CONVEX, "PCG met p'Kp <= 0 (K not positive definite)");
+  if (err == 8) return kq_fail(h, KQ_ERR_NUMERIC, "PCG met NaN");
+  if (err != 0) return kq_fail(h, KQ_ERR_CUDA, "PCG kernel error flag " + std::to_string(err));
+  return KQ_OK;
+}
+
+double dev_norm(kq_problem *h, const double *v, int64_t N) {
+  const int nb = 256;
+  k_sumsq<<<nb, 256, 0, h->stream>>>(N, v, h->red);
+  k_final_sum<<<1, 256, 0, h->stream>>>(nb, h->red, h->red_out);
+  cudaMemcpyAsync(h->h_red, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  return sqrt(h->h_red[0]);
+}
+
+}  // namespace
+
+double pcg_last_kernel_ms() { return g_last_ms; }
+
+kq_status pcg_setup(kq_problem *h, int grid_ctas) {
+  PcgWork &W = h->W;
+  const DevProb &P = h->P;
+  const int64_t n = P.n, nkp = P.nkp;
+  int threads = 512;
+  size_t smem = 0;
+  int win_cap = 0;
+  if (P.hkind == KQ_H_DENSE) {
+    threads = 512;
+    win_cap = (int)n;
+    smem = (size_t)2 * n * sizeof(double);
+    if (smem > 200 * 1024)
+      return kq_fail(h, KQ_ERR_ARG, "dense H: n too large for the single-problem kernel");
+  }
+  int sms = h->num_sms;
+  // provisional grid for the partition
+  int G = grid_ctas > 0 ? grid_ctas : sms;
+  if (P.hkind == KQ_H_DENSE) {
+    // small dense problems are latency-bound: fewer CTAs, cheaper barriers
+    const int64_t rows = n + P.m + P.me;
+    const int64_t want = ceil_div64(rows, (int64_t)(threads / 32) * 2);
+    G = grid_ctas > 0 ? grid_ctas : (int)std::max<int64_t>(1, std::min<int64_t>(sms, want));
+  }
+  W.row_begin = dalloc<int64_t>(h, G + 1);
+  W.win_lo = dalloc<int32_t>(h, G);
+  W.win_hi = dalloc<int32_t>(h, G);
+  if (!W.row_begin || !W.win_lo || !W.win_hi) return kq_fail(h, KQ_ERR_OOM, "pcg partition");
+  std::vector<int64_t> rb(G + 1, 0);
+  if (P.hkind == KQ_H_CSR_LSQ) {
+    std::vector<int64_t> rp(P.nP + 1);
+    KQ_CUDA(h, cudaMemcpy(rp.data(), P.rowptr, (P.nP + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    const int64_t nnz = rp[P.nP];
+    for (int c = 0; c <= G; ++c) {
+      const int64_t target = (nnz * c) / G;
+      rb[c] = std::lower_bound(rp.begin(), rp.end(), target) - rp.begin();
+      if (rb[c] > P.nP) rb[c] = P.nP;
+    }
+    rb[0] = 0;
+    rb[G] = P.nP;
+    for (int c = 1; c <= G; ++c) rb[c] = std::max(rb[c], rb[c - 1]);
+  } else {
+    const int64_t rows = (P.hkind == KQ_H_LOWRANK) ? n : 0;
+    for (int c = 0; c <= G; ++c) rb[c] = rows * c / G;
+  }
+  KQ_CUDA(h, cudaMemcpy(W.row_begin, rb.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  if (P.hkind == KQ_H_CSR_LSQ) {
+    k_windows<<<G, 256, 0, h->stream>>>(P.rowptr, P.col, W.row_begin, W.win_lo, W.win_hi);
+    KQ_CUDA(h, cudaGetLastError());
+    std::vector<int32_t> lo(G), hi(G);
+    KQ_CUDA(h, cudaMemcpyAsync(lo.data(), W.win_lo, G * 4, cudaMemcpyDeviceToHost, h->stream));
+    KQ_CUDA(h, cudaMemcpyAsync(hi.data(), W.win_hi, G * 4, cudaMemcpyDeviceToHost, h->stream));
+    KQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    int wmax = 0;
+    for (int c = 0; c < G; ++c) wmax = std::max(wmax, hi[c] - lo[c]);
+    const int cap_elems = (int)(160 * 1024 / (2 * sizeof(double)));
+    win_cap = std::min(wmax, cap_elems);
+    smem = (size_t)2 * win_cap * sizeof(double);
+  } else if (P.hkind == KQ_H_LOWRANK) {
+    int64_t rmax = 0;
+    for (int c = 0; c < G; ++c) rmax = std::max(rmax, rb[c + 1] - rb[c]);
+    win_cap = (int)rmax;
+    smem = (size_t)rmax * sizeof(double) + (size_t)(P.k + P.me + 1) * sizeof(double) +
+           (size_t)(P.me + 1) * sizeof(double) + 64;
+    if (smem > 200 * 1024) return kq_fail(h, KQ_ERR_ARG, "lowrank: too many rows per CTA");
+  }
+  W.G = G;
+  W.threads = threads;
+  W.win_cap = win_cap;
+  W.smem = smem;
+  // verify co-residency for the cooperative launch
+  {
+    int per_sm = 0;
+    const void *f = (const void *)pick_kernel<double>(P);
+    KQ_CUDA(h, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, threads, smem));
+    if (per_sm * sms < G)
+      return kq_fail(h, KQ_ERR_ARG, "persistent PCG grid does not fit on the device");
+    const void *f32 = (const void *)pick_kernel<float>(P);
+    KQ_CUDA(h, cudaFuncSetAttribute(f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    KQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32, threads, smem));
+    if (per_sm * sms < G)
+      return kq_fail(h, KQ_ERR_ARG, "persistent PCG grid (mixed) does not fit on the device");
+  }
+  W.r = dalloc<double>(h, nkp);
+  W.y = dalloc<double>(h, nkp);
+  W.pb0 = dalloc<double>(h, nkp);
+  W.pb1 = dalloc<double>(h, nkp);
+  W.qlam = dalloc<double>(h, nkp - n + 1);
+  W.accx64 = dalloc<double>(h, n);
+  W.accx32 = dalloc<float>(h, n);
+  W.g64 = dalloc<double>(h, P.k + P.me + 1);
+  W.slots = dalloc<double>(h, 4 * G);
+  W.bar = dalloc<unsigned int>(h, 2);
+  W.err = dalloc<int>(h, 1);
+  W.iters = dalloc<int>(h, 1);
+  W.resn = dalloc<double>(h, 2);
+  if (!W.r || !W.y || !W.pb0 || !W.pb1 || !W.qlam || !W.accx64 || !W.accx32 || !W.g64 ||
+      !W.slots || !W.bar || !W.err || !W.iters || !W.resn)
+    return kq_fail(h, KQ_ERR_OOM, "pcg work space");
+  KQ_CUDA(h, cudaMemset(W.accx64, 0, n * sizeof(double)));
+  KQ_CUDA(h, cudaMemset(W.accx32, 0, n * sizeof(float)));
+  KQ_CUDA(h, cudaMallocHost((void **)&W.h_pinned, 64));
+  return KQ_OK;
+}
+
+kq_status pcg_apply(kq_problem *h, const double *v, double *out, int prec, float *ms) {
+  kq_status st = launch(h, prec, v, out, 0.0, 0, 1, nullptr, nullptr, nullptr);
+  if (ms) *ms = g_last_ms;
+  return st;
+}
+
+// Jacobi PCG with optional FP32-matvec correction solves and FP64 residual
+// refinement:  z = 0;  repeat { solve K dz = res (FP32 products for the first
+// refine_steps passes, FP64 afterwards);  z += dz;  res = rhs - K z in FP64 }
+// until |res| <= tol |rhs| or the iteration budget is spent.
+kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_opts &o,
+                    kq_pcg_stats *st) {
+  const int64_t N = h->P.nkp;
+  kq_pcg_stats s{};
+  const double bn = dev_norm(h, rhs, N);
+  KQ_CUDA(h, cudaMemsetAsync(z, 0, N * sizeof(double), h->stream));
+  if (!(bn > 0.0)) {
+    s.status = (bn == 0.0) ? KQ_OK : KQ_ERR_NUMERIC;
+    if (st) *st = s;
+    return s.status == KQ_OK ? KQ_OK : kq_fail(h, KQ_ERR_NUMERIC, "rhs has NaN/Inf");
+  }
+  double *res = h->tmp, *dz = h->zref;
+  KQ_CUDA(h, cudaMemcpyAsync(res, rhs, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  double resn = bn;
+  int total = 0;
+  const int mixed = o.precision == KQ_PREC_MIXED;
+  const int max_passes = (mixed ? o.refine_steps : 0) + 3;
+  kq_status rc = KQ_OK;
+  for (int pass = 0; pass < max_passes; ++pass) {
+    const int prec = (mixed && pass < o.refine_steps) ? KQ_PREC_MIXED : KQ_PREC_F64;
+    double rel = o.tol * bn / resn;
+    if (prec == KQ_PREC_MIXED) rel = std::max(rel, o.inner_tol);
+    rel = std::min(rel, 0.5);
+    const int budget = o.maxit - total;
+    if (budget <= 0) break;
+    int it = 0;
+    rc = launch(h, prec, res, dz, rel, budget, 0, &it, nullptr, nullptr);
+    s.kernel_ms += g_last_ms;
+    total += it;
+    s.passes++;
+    if (rc != KQ_OK) break;
+    k_add<<<256, 256, 0, h->stream>>>(N, z, dz);
+    float ms = 0.f;
+    rc = pcg_apply(h, z, dz, KQ_PREC_F64, &ms);
+    s.kernel_ms += ms;
+    if (rc != KQ_OK) break;
+    const int nb = 256;
+    k_axpy_res<<<nb, 256, 0, h->stream>>>(N, rhs, dz, res, h->red);
+    k_final_sum<<<1, 256, 0, h->stream>>>(nb, h->red, h->red_out);
+    KQ_CUDA(h, cudaMemcpyAsync(h->h_red, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    KQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    resn = sqrt(h->h_red[0]);
+    if (!(resn == resn)) { rc = kq_fail(h, KQ_ERR_NUMERIC, "PCG residual is NaN"); break; }
+    if (resn <= o.tol * bn) break;
+    if (total >= o.maxit) break;
+  }
+  s.iters = total;
+  s.rel_res = resn / bn;
+  if (rc == KQ_OK && resn > o.tol * bn) rc = KQ_WARN_PCG_MAXIT;
+  s.status = rc;
+  if (st) *st = s;
+  return rc;
+}

@@ -139,7 +139,7 @@ def dense_qp(n: int = 200, m: int = 100, q: Optional[int] = None, seed: int = 0,
     u = rng.uniform(0.1, 1.0, m)
     H = Q.T @ Q / q + 1e-2 * np.eye(n)
     H = 0.5 * (H + H.T)
-    meta = {"seed": seed, "q": q}
+    meta = {"seed": seed, "q": q, "a_f32": a_f32}
     if h_bf16:
         bits = to_bf16_bits(H)
         H = from_bf16_bits(bits).reshape(n, n)

@@ -1,0 +1,180 @@
+"""GPU parity: every step of the CUDA path against the FP64 CPU oracle on the
+same seeded inputs, through the C ABI.
+
+Tolerances (derivation): the FP64 path evaluates the same sums as the oracle
+in a different order, so single products agree to a few ulps of the largest
+term, well below 1e-11 relative; the mixed path rounds the matrix-vector
+product to FP32 (unit roundoff 6e-8) over at most a few hundred terms per
+entry, so 1e-5 relative is a safe bound.  Solves are compared through their
+FP64 residuals (a property that holds at any size) and, where the system is
+well conditioned, against the direct solution.  IPM results use the gate of
+the acceptance metrics: objective within 1e-6 relative and KKT_rel <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import qpgen
+from oracle import ipm as I
+from tests.gpu_helpers import from_padded, random_state, relerr, set_gpu_state, to_padded
+
+pytestmark = pytest.mark.gpu
+
+PROBLEMS = {
+    "dense_eq": lambda: qpgen.tiny_qp(37, 23, 5, me=2),
+    "dense_onesided": lambda: qpgen.dense_qp(70, 45, seed=3),
+    "csr": lambda: qpgen.dose_qp(3000, 300, 30, 40, 150, seed=8),
+    "lowrank": lambda: qpgen.svm_qp(500, 16, seed=9),
+}
+
+
+@pytest.fixture(scope="module")
+def kq():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2308_00637_gb300 as m
+    m.load()
+    return m
+
+
+def _setup(kq, name, seed=0, mu=0.01):
+    qp = PROBLEMS[name]()
+    S = I.scale(qp)
+    st = random_state(S, seed)
+    h = kq.create_from(qp)
+    set_gpu_state(kq, h, S, st, mu)
+    return qp, S, st, h
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_scaling_matches(kq, name):
+    qp = PROBLEMS[name]()
+    S = I.scale(qp)
+    h = kq.create_from(qp)
+    sigma, rhoA, rhoC = kq.qp_scaling(h)
+    assert sigma == pytest.approx(S.sigma, rel=1e-13)
+    assert relerr(rhoA, S.rhoA) <= 1e-13
+    assert relerr(rhoC, S.rhoC) <= 1e-13
+
+
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_residuals_rhs_diag(kq, name):
+    qp, S, st, h = _setup(kq, name)
+    mu = 0.01
+    n, m, me = S.n, S.m, S.me
+    bufs = {k: np.zeros(n) for k in ("r_H", "r_lx", "r_ux", "r_c3", "r_c4")}
+    bufs.update({k: np.zeros(m) for k in ("r_lA", "r_uA", "r_c1", "r_c2")})
+    bufs["r_e"] = np.zeros(me)
+    bufs["rhs"] = np.zeros(n + me + 2 * m)
+    norm = kq.qp_residuals(h, **bufs)
+    r = I.residuals(S, st, mu)
+    assert relerr(bufs["r_H"], r["r_H"]) <= 1e-11
+    assert relerr(bufs["r_lA"][S.L], r["r_lA"]) <= 1e-11
+    assert relerr(bufs["r_uA"][S.U], r["r_uA"]) <= 1e-11
+    assert relerr(bufs["r_c1"][S.L], r["r_c1"]) <= 1e-11
+    assert relerr(bufs["r_lx"][S.Lx], r["r_lx"]) <= 1e-11
+    assert relerr(bufs["r_c4"][S.Ux], r["r_c4"]) <= 1e-11
+    assert relerr(bufs["r_e"], r["r_e"]) <= 1e-11
+    assert norm == pytest.approx(I.residual_norm(r), rel=1e-11)
+    dg, D, r1, r2 = I.reduced_system(S, st, r, mu)
+    rhs = I.doubly_augmented_rhs(S, D, r1, r2)
+    assert relerr(from_padded(S, bufs["rhs"]), rhs) <= 1e-11
+    diag = np.zeros(n + me + 2 * m)
+    kq.kkt_diag(h, diag)
+    assert relerr(from_padded(S, diag), I.jacobi_diagonal(S, dg, D)) <= 1e-11
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 1e-5)], ids=["f64", "mixed"])
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_kkt_apply(kq, name, prec, tol):
+    qp, S, st, h = _setup(kq, name, seed=1)
+    mu = 0.01
+    r = I.residuals(S, st, mu)
+    dg, D, _, _ = I.reduced_system(S, st, r, mu)
+    v = np.random.default_rng(5).standard_normal(S.NK)
+    ref = I.kkt_apply(S, dg, D, v)
+    out = np.zeros(h.nkp)
+    kq.kkt_apply(h, to_padded(S, v), out, prec)
+    assert relerr(from_padded(S, out), ref) <= tol
+    # padded rows of absent bounds stay exactly zero
+    pad = np.ones(h.nkp, bool)
+    pad[np.concatenate([np.arange(S.n + S.me), S.n + S.me + S.L, S.n + S.me + S.m + S.U])] = False
+    assert np.all(out[pad] == 0.0)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["f64", "mixed"])
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_kkt_pcg_solve(kq, name, prec):
+    qp, S, st, h = _setup(kq, name, seed=2)
+    mu = 0.01
+    r = I.residuals(S, st, mu)
+    dg, D, r1, r2 = I.reduced_system(S, st, r, mu)
+    rhs = I.doubly_augmented_rhs(S, D, r1, r2)
+    sol = np.zeros(h.nkp)
+    opts = kq.default_pcg_opts(tol=1e-10, maxit=20000, precision=prec, refine_steps=3,
+                               inner_tol=1e-5)
+    rc, stt = kq.kkt_pcg_solve(h, to_padded(S, rhs), sol, opts)
+    z = from_padded(S, sol)
+    # FP64 residual of the returned solution, evaluated by the oracle
+    res = np.linalg.norm(rhs - I.kkt_apply(S, dg, D, z)) / np.linalg.norm(rhs)
+    assert res <= 1e-10 * 1.01, (res, stt.as_dict())
+    dx, dl = I.newton_direct(S, dg, D, r1, r2)
+    zs = np.concatenate([dx, dl])
+    assert relerr(z, zs) <= 1e-6
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["f64", "mixed"])
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_ipm_matches_oracle(kq, name, prec):
+    qp = PROBLEMS[name]()
+    res = oracle.ipm_solve(qp)
+    assert res.status == "converged"
+    opts = kq.default_ipm_opts(precision=prec)
+    rc, st, out = kq.solve(qp, opts)
+    f_gpu, f_ref = qp.objective(out["x"]), qp.objective(res.x)
+    assert abs(f_gpu - f_ref) <= 1e-6 * (1 + abs(f_ref)), (f_gpu, f_ref, st.as_dict())
+    met = oracle.kkt_metrics(qp, out["x"], out["lam_lA"], out["lam_uA"], out["lam_lx"],
+                             out["lam_ux"], out["lam_e"])
+    assert met["kkt_rel"] <= 1e-6, met
+    assert st.mu_final == pytest.approx(res.mu)
+
+
+def test_config0(kq):
+    """Tiny dense convex QP (n=200, 100 one-sided rows, box bounds)."""
+    qp = qpgen.config0()
+    res = oracle.ipm_solve(qp)
+    for prec in (0, 1):
+        rc, st, out = kq.solve(qp, kq.default_ipm_opts(precision=prec))
+        f_gpu, f_ref = qp.objective(out["x"]), qp.objective(res.x)
+        assert abs(f_gpu - f_ref) <= 1e-6 * (1 + abs(f_ref))
+        met = oracle.kkt_metrics(qp, out["x"], out["lam_lA"], out["lam_uA"], out["lam_lx"],
+                                 out["lam_ux"], out["lam_e"])
+        assert met["kkt_rel"] <= 1e-6
+
+
+def test_unconstrained_closed_form(kq):
+    qp = qpgen.dense_qp(50, 1, seed=4)
+    qp.akind, qp.A, qp.lA, qp.uA = "none", None, None, None
+    qp.lx = np.full(qp.n, -np.inf)
+    qp.ux = np.full(qp.n, np.inf)
+    rc, st, out = kq.solve(qp)
+    xs = -np.linalg.solve(qp.H_dense(), qp.p)
+    assert relerr(out["x"], xs) <= 1e-9
+
+
+def test_bad_arguments_are_rejected(kq):
+    import ctypes
+    H = kq.KqHop()
+    H.kind = 7
+    with pytest.raises(kq.KQError) as e:
+        kq.qp_create(4, H, np.zeros(4))
+    assert e.value.status == kq.KQ_ERR_ARG
+    with pytest.raises(kq.KQError):
+        kq.qp_create(0, kq.KqHop(), np.zeros(1))
+
+
+def test_backward_before_solve_is_a_state_error(kq):
+    h = kq.create_from(qpgen.dense_qp(10, 5, seed=1))
+    with pytest.raises(kq.KQError) as e:
+        kq.qp_backward(h, np.ones(10), np.zeros(10))
+    assert e.value.status == kq.KQ_ERR_STATE
