@@ -1,0 +1,382 @@
+"""Benchmark: time-to-1e-6 of the Krylov IPM on the dose-shaped QP
+(P 200k x 20k CSR, 2e7 nnz, 10k two-sided dose-limit rows, x >= 0).
+
+One step = one full ipm_solve (Algorithm 1: residuals, right-hand side,
+Jacobi diagonal, persistent PCG solves, step recovery, ratio test, update,
+mu rule) from the initial point to mu < 1e-6, inputs resident in HBM.
+``e2e`` repeats the step through the C ABI with host buffers: qp_create from
+host arrays (upload inside the timed region), ipm_solve writing the solution
+to host arrays, qp_destroy.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|f64]
+        python bench.py --impl reference      (oracle arm, host cores)
+        python bench.py --mode pcg --pcg-iters 200   (one PCG launch, for ncu)
+Under torchrun (N > 1) every rank solves its own replica of the problem (the
+method does not shard; replicas only) and value is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ALGO_BYTES_NOTE = ("per K*v product: nnz*(4 B value + 4 B column) + (rows+1)*4 B row pointer "
+                   "+ rows*4 B weight")
+WORKLOAD = "dose_qp_200k_x_20k_nnz2e7"
+COUNTS_FILE = os.path.join(ROOT, "profiles", "dose200k_counts.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pcg_csr_dose200k_traffic.json")
+
+
+def algo_bytes(qp) -> float:
+    rows, nnz = qp.P.shape[0], qp.P.nnz
+    return nnz * 8.0 + (rows + 1) * 4.0 + rows * 4.0
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in ("pcg.cu", "common.cuh", "kq_internal.h"):
+        h.update(open(os.path.join(ROOT, "paper_2308_00637_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def read_peaks():
+    try:
+        pk = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(pk["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks during the timed region (started before, stopped after)."""
+
+    def __init__(self, dev: int):
+        self.dev = dev
+        self.proc = None
+        self.path = tempfile.mktemp(suffix=".csv")
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        try:
+            rows = [l.split(",") for l in open(self.path).read().strip().splitlines() if l.strip()]
+        except Exception:
+            rows = []
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = max(mx, float(r[1]))
+                for nm, v in zip(names, r[4:8]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        sm.sort()
+        med = sm[len(sm) // 2] if sm else None
+        return {"sm_mhz": med, "sm_max_mhz": mx or None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+CPU_SAMPLE_CODE = r"""
+import json, sys, time, os
+sys.path.insert(0, {root!r})
+import numpy as np
+import qpgen
+from oracle import ipm as I
+qp = qpgen.config1()
+S = I.scale(qp)
+st = I.initial_point(S)
+t0 = time.perf_counter()
+r = I.residuals(S, st, 1.0)
+dg, D, r1, r2 = I.reduced_system(S, st, r, 1.0)
+rhs = I.doubly_augmented_rhs(S, D, r1, r2)
+diag = I.jacobi_diagonal(S, dg, D)
+t_ipm = time.perf_counter() - t0
+nit = {nit}
+t0 = time.perf_counter()
+z, it, _ = I.pcg_reference(lambda v: I.kkt_apply(S, dg, D, v), rhs, diag, 0.0, nit)
+t_pcg = (time.perf_counter() - t0) / (it + 1)
+print(json.dumps({{"t_ipm": t_ipm, "t_prod": t_pcg, "iters": it}}))
+"""
+
+
+def cpu_oracle_sample(nit: int):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", CPU_SAMPLE_CODE.format(root=ROOT, nit=nit)],
+                         capture_output=True, text=True, env=env, timeout=600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def load_counts():
+    try:
+        c = json.load(open(COUNTS_FILE))
+        return int(c["ipm_iters"]), int(c["pcg_products"]), "recorded GPU run"
+    except Exception:
+        return 26, 50000, "estimate"
+
+
+def cpu_baseline_line(ipm_iters, products, nit=40):
+    s = cpu_oracle_sample(nit)
+    val = s["t_ipm"] * 2 * ipm_iters + s["t_prod"] * products
+    return {"value": val, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": (f"{s['iters']} reference-PCG iterations (oracle.pcg_reference, FP64, "
+                       f"matrix-free K*v) plus one residual/RHS/diagonal evaluation at the "
+                       f"initial iterate of the 200k x 20k dose QP, 1 thread; extrapolated to "
+                       f"{ipm_iters} IPM iterations (2 evaluations each) and {products} K*v "
+                       f"products"),
+            "t_per_product_s": s["t_prod"], "t_per_eval_s": s["t_ipm"]}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    ipm_iters, products, src = load_counts()
+    vals = []
+    for _ in range(args.warmup):
+        cpu_oracle_sample(5)
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline_line(ipm_iters, products, nit=10)
+        vals.append(last["value"])
+    v = sum(vals) / len(vals)
+    line = {"impl": "reference", "metric": "time-to-1e-6 IPM solve", "value": v, "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "counts_from": src},
+            "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": last["sample"], "value": v,
+                             "unit": "s"},
+            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--mode", default="solve", choices=["solve", "pcg"])
+    ap.add_argument("--pcg-iters", type=int, default=200)
+    ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--write-counts", default=None)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    import qpgen
+    import paper_2308_00637_gb300 as kq
+    from paper_2308_00637_gb300 import build as kqbuild
+    if rank == 0:
+        kqbuild.build()
+    if dist is not None:
+        dist.barrier()
+    kq.load()
+
+    qp = qpgen.config1()
+    prec = kq.KQ_PREC_MIXED if args.precision == "mixed" else kq.KQ_PREC_F64
+    opts = kq.default_ipm_opts(precision=prec)
+    h = kq.create_from(qp, device_tensors=True)
+    n, m = h.n, h.m
+    dev = {k: torch.zeros(s, dtype=torch.float64, device="cuda")
+           for k, s in (("x", n), ("lam_lA", m), ("lam_uA", m), ("lam_lx", n), ("lam_ux", n))}
+
+    if args.mode == "pcg":
+        # one Newton system at the initial point, fixed iteration count (profiling)
+        rhs = torch.zeros(h.nkp, dtype=torch.float64, device="cuda")
+        sol = torch.zeros_like(rhs)
+        kq.qp_residuals(h, rhs=rhs)
+        po = kq.default_pcg_opts(tol=1e-30, maxit=args.pcg_iters, precision=prec,
+                                 refine_steps=1 if prec else 0, inner_tol=1e-30)
+        for _ in range(max(1, args.steps)):
+            kq.kkt_pcg_solve(h, rhs, sol, po)
+        torch.cuda.synchronize()
+        print(json.dumps({"mode": "pcg", "iters": args.pcg_iters}))
+        return 0
+
+    def solve():
+        return kq.ipm_solve(h, opts, **dev, allow=(kq.KQ_OK,))[1]
+
+    for _ in range(args.warmup):
+        solve()
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    stats = []
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            stats.append(solve())
+        e1.record(stream)
+        torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    t_step = ms_total / 1e3 / args.steps
+    if dist is not None:
+        t = torch.tensor([t_step], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = float(t.item())
+    s0 = stats[-1]
+    prod = sum(s.pcg_products for s in stats)
+    kms = sum(s.pcg_kernel_ms for s in stats)
+    launches = sum(s.pcg_launches for s in stats)
+    abytes = algo_bytes(qp)
+    achieved = prod * abytes / (kms * 1e-3) / 1e9
+    peak, peak_src = read_peaks()
+    traffic = None
+    try:
+        tr = json.load(open(TRAFFIC_FILE))
+        if tr.get("kernel_hash") == kernel_source_hash() and tr.get("precision") == args.precision:
+            traffic = tr["dram_bytes_per_launch_product"] * (prod / max(1, launches))
+    except Exception:
+        traffic = None
+    # accuracy of the result (original units), checked by the CPU oracle's metric code
+    x = dev["x"].cpu().numpy()
+    out = {k: v.cpu().numpy() for k, v in dev.items()}
+    import oracle
+    met = oracle.kkt_metrics(qp, x, out["lam_lA"], out["lam_uA"], out["lam_lx"], out["lam_ux"],
+                             np.zeros(0))
+
+    # ---- e2e: host buffers through the public API, copies inside the timed region
+    host_in = [qp.P.data, qp.P.indices, qp.P.indptr, qp.w, qp.p, qp.a_rows, qp.lA, qp.uA,
+               qp.lx, qp.ux]
+    h2d = int(sum(np.asarray(a).nbytes for a in host_in))
+    hout = {k: np.zeros(v.numel()) for k, v in dev.items()}
+    d2h = int(sum(a.nbytes for a in hout.values()))
+    kq.qp_destroy(h)
+    torch.cuda.synchronize()
+    e2e_times = []
+    for _ in range(max(1, args.e2e_steps)):
+        t0 = time.perf_counter()
+        h2 = kq.create_from(qp)          # host numpy buffers -> device copies
+        kq.ipm_solve(h2, opts, **hout)
+        kq.qp_destroy(h2)
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+    e2e = sum(e2e_times) / len(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = float(t.item())
+
+    # ---- plain-FP64 form on the same problem, for the comparison
+    cmp = None
+    if not args.no_compare and rank == 0:
+        other = kq.KQ_PREC_F64 if prec == kq.KQ_PREC_MIXED else kq.KQ_PREC_MIXED
+        h3 = kq.create_from(qp, device_tensors=True)
+        torch.cuda.synchronize()
+        ec0, ec1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ec0.record(stream)
+        rc3, s3 = kq.ipm_solve(h3, kq.default_ipm_opts(precision=other), **dev,
+                               allow=(kq.KQ_OK, kq.KQ_ERR_IPM_MAXIT))
+        ec1.record(stream)
+        torch.cuda.synchronize()
+        cmp = {"precision": "f64" if other == kq.KQ_PREC_F64 else "mixed",
+               "time_s": ec0.elapsed_time(ec1) / 1e3, "status": int(rc3),
+               "ipm_iters": s3.ipm_iters, "pcg_iters": int(s3.pcg_iters),
+               "pcg_kernel_ms": s3.pcg_kernel_ms,
+               "kv_gbs": s3.pcg_products * abytes / (s3.pcg_kernel_ms * 1e-3) / 1e9}
+        kq.qp_destroy(h3)
+
+    if args.write_counts and rank == 0:
+        json.dump({"ipm_iters": s0.ipm_iters, "pcg_products": int(s0.pcg_products),
+                   "pcg_iters": int(s0.pcg_iters), "precision": args.precision},
+                  open(args.write_counts, "w"), indent=1)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        try:
+            cpu = cpu_baseline_line(s0.ipm_iters, int(s0.pcg_products))
+        except Exception as e:   # reported, not fatal
+            cpu = {"error": str(e)[-300:]}
+
+    if rank == 0:
+        line = {
+            "metric": "time-to-1e-6 IPM solve (dose-shaped QP, PCG on the doubly augmented KKT system)",
+            "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32-matvec/f64" if prec == kq.KQ_PREC_MIXED else "f64",
+            "data": "synthetic (seeded generator, seed 1)",
+            "config": {"workload": WORKLOAD, "rows": qp.P.shape[0], "n": qp.n, "nnz": qp.P.nnz,
+                       "dose_limit_rows": m, "precision": args.precision,
+                       "l2": "inputs larger than L2 (P is 160 MB > 129 MB)",
+                       "parallelism": "replicas" if world > 1 else "single-gpu"},
+            "ipm_iters": s0.ipm_iters, "pcg_iters": int(s0.pcg_iters),
+            "pcg_products": int(s0.pcg_products), "pcg_maxit_hits": s0.pcg_maxit_hits,
+            "pcg_iters_per_s": s0.pcg_iters / t_step,
+            "kkt_rel": met["kkt_rel"], "objective": met["objective"],
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "peak_source": peak_src,
+                         "kernel": "pcg_kernel<OpCsr> (persistent PCG solve)",
+                         "algorithmic_bytes_per_product": abytes, "note": ALGO_BYTES_NOTE},
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(sum(s.kernel_launches for s in stats)),
+            "clocks": clk.summary(),
+            "compare": cmp,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line))
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

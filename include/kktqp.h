@@ -101,6 +101,7 @@ typedef struct {
   double inner_tol;        /* MIXED: relative tolerance of each FP32 solve      */
   double timeout_s;        /* device barrier budget per wait (seconds)         */
   int grid_ctas;           /* 0 = auto; else persistent-kernel grid size        */
+  int verbose;             /* 1 = one line per IPM iteration on stderr          */
 } kq_ipm_opts;
 
 typedef struct {
@@ -115,6 +116,8 @@ typedef struct {
   double pcg_time_s;       /* device time inside PCG solves (CUDA events)       */
   double pcg_kernel_ms;    /* device time of the persistent PCG kernels only    */
   long long pcg_launches;  /* persistent PCG kernel launches                    */
+  long long pcg_products;  /* K*v products inside PCG kernels (iterations+applies)*/
+  long long kernel_launches; /* all kernels this call launched                   */
 } kq_ipm_stats;
 
 typedef struct {

@@ -441,8 +441,12 @@ def newton_direct(S: Scaled, dg, D, r1, r2, solver: str = "auto"):
             Msp = Msp + sp.csr_matrix(S.C.T @ (S.C / D[:me, None]))
         Mc = Msp.tocoo()
         u = int(np.max(np.abs(Mc.row - Mc.col))) if Mc.nnz else 0
-        ab = _banded_upper(Msp, u)
-        dx = sla.solveh_banded(ab, rhs, lower=False)
+        if 4 * u > n:
+            # wide band: plain dense Cholesky of the same Schur complement
+            dx = sla.cho_solve(sla.cho_factor(Msp.toarray(), lower=False), rhs)
+        else:
+            ab = _banded_upper(Msp, u)
+            dx = sla.solveh_banded(ab, rhs, lower=False)
     elif solver == "schur_woodbury":
         # Q + B'D^-1B = diag(dg) + Z Z' + C' D_e^-1 C  (no general rows)
         assert S.hkind == "lowrank" and S.m == 0

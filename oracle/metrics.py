@@ -12,8 +12,9 @@ evaluated in float64 from the original problem data and a candidate solution
 * dual_rel   = ||H x + p - A'(lam_lA - lam_uA) - (lam_lx - lam_ux) - C' lam_e||_inf
                over 1 + max(||Hx||_inf, ||p||_inf, ||A'(lam_lA - lam_uA)||_inf,
                ||lam_lx - lam_ux||_inf, ||C' lam_e||_inf);
-* compl_rel  = max_i |lam_i * shat_i| / (1 + |f(x)|), shat the slack recomputed
-               from x;
+* compl_rel  = max_i |lam_i * shat_i| / (1 + max(|x'Hx/2|, |p'x|)), shat the
+               slack recomputed from x (the magnitude of the objective's terms,
+               not of their sum, which can cancel);
 * kkt_rel    = max of the three.
 """
 from __future__ import annotations
@@ -82,6 +83,7 @@ def kkt_metrics(qp, x, lam_lA, lam_uA, lam_lx, lam_ux, lam_e):
     dual = float(np.max(np.abs(rH))) / scale
 
     f = float(0.5 * x @ Hx + qp.p @ x)
+    fscale = max(abs(0.5 * float(x @ Hx)), abs(float(qp.p @ x)))
     comp = [0.0]
     if m:
         with np.errstate(invalid="ignore"):
@@ -94,7 +96,7 @@ def kkt_metrics(qp, x, lam_lA, lam_uA, lam_lx, lam_ux, lam_e):
         sux = np.where(np.isfinite(ux), ux - x, 0.0)
     comp.append(float(np.max(np.abs(np.asarray(lam_lx) * slx))))
     comp.append(float(np.max(np.abs(np.asarray(lam_ux) * sux))))
-    compl = max(comp) / (1.0 + abs(f))
+    compl = max(comp) / (1.0 + fscale)
     return {"primal_rel": primal, "dual_rel": dual, "compl_rel": compl,
             "kkt_rel": max(primal, dual, compl), "objective": f}
 

@@ -48,7 +48,7 @@ class KqIpmOpts(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mu0", C.c_double), ("mu_tol", C.c_double),
                 ("ipm_maxit", C.c_int), ("pcg_tol", C.c_double), ("pcg_maxit", C.c_int),
                 ("precision", C.c_int), ("refine_steps", C.c_int), ("inner_tol", C.c_double),
-                ("timeout_s", C.c_double), ("grid_ctas", C.c_int)]
+                ("timeout_s", C.c_double), ("grid_ctas", C.c_int), ("verbose", C.c_int)]
 
 
 class KqIpmStats(C.Structure):
@@ -56,7 +56,8 @@ class KqIpmStats(C.Structure):
                 ("res_norm", C.c_double), ("primal_inf", C.c_double), ("dual_inf", C.c_double),
                 ("compl_inf", C.c_double), ("pcg_iters", C.c_longlong),
                 ("pcg_maxit_hits", C.c_int), ("time_s", C.c_double), ("pcg_time_s", C.c_double),
-                ("pcg_kernel_ms", C.c_double), ("pcg_launches", C.c_longlong)]
+                ("pcg_kernel_ms", C.c_double), ("pcg_launches", C.c_longlong),
+                ("pcg_products", C.c_longlong), ("kernel_launches", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "kq_internal.h"
 #include <chrono>
+#include <cstdio>
 #include <cstring>
 #include <vector>
 
@@ -546,6 +547,7 @@ kq_status rowdot(kq_problem *h, const double *v, double *t, double *tC) {
     k_rowdot_dense<float><<<NB, NT, 0, h->stream>>>(P, v, t, tC);
   else
     k_rowdot_dense<double><<<NB, NT, 0, h->stream>>>(P, v, t, tC);
+  ++h->launches;
   KQ_CUDA(h, cudaGetLastError());
   return KQ_OK;
 }
@@ -556,19 +558,25 @@ kq_status hx_apply(kq_problem *h, const double *v, double *hx) {
     if (P.hdtype == KQ_F64) k_hx_dense<double><<<NB, NT, 0, h->stream>>>(P, v, hx);
     else if (P.hdtype == KQ_F32) k_hx_dense<float><<<NB, NT, 0, h->stream>>>(P, v, hx);
     else k_hx_dense<__nv_bfloat16><<<NB, NT, 0, h->stream>>>(P, v, hx);
+    ++h->launches;
   } else if (P.hkind == KQ_H_LOWRANK) {
     KQ_CUDA(h, cudaMemsetAsync(h->g, 0, P.k * sizeof(double), h->stream));
     const int nbz = (int)std::min<int64_t>(1024, std::max<int64_t>(1, P.n / 64));
     if (P.hdtype == KQ_F64) {
       k_zt<double><<<nbz, 256, 0, h->stream>>>(P, v, h->g);
+      ++h->launches;
       k_zg<double><<<NB, NT, 0, h->stream>>>(P, h->g, hx);
+      ++h->launches;
     } else {
       k_zt<float><<<nbz, 256, 0, h->stream>>>(P, v, h->g);
+      ++h->launches;
       k_zg<float><<<NB, NT, 0, h->stream>>>(P, h->g, hx);
+      ++h->launches;
     }
   } else {
     // CSR: H x is produced by the scatter pass; here y = P x
     k_csr_rowdot<<<NB, NT, 0, h->stream>>>(P, v, h->yP);
+    ++h->launches;
     KQ_CUDA(h, cudaMemsetAsync(hx, 0, P.n * sizeof(double), h->stream));
   }
   KQ_CUDA(h, cudaGetLastError());
@@ -582,6 +590,7 @@ kq_status fetch(kq_problem *h, int ncols, std::vector<int> mins, double *out) {
   memcpy(hf, flags, sizeof flags);
   KQ_CUDA(h, cudaMemcpyAsync(h->dflags, hf, 8 * sizeof(int), cudaMemcpyHostToDevice, h->stream));
   k_reduce_cols<<<1, 256, 0, h->stream>>>(NB, ncols, h->red, h->dflags, h->red_out);
+  ++h->launches;
   KQ_CUDA(h, cudaMemcpyAsync(h->h_red, h->red_out, ncols * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   KQ_CUDA(h, cudaStreamSynchronize(h->stream));
   for (int c = 0; c < ncols; ++c) out[c] = h->h_red[c];
@@ -592,11 +601,13 @@ kq_status fetch(kq_problem *h, int ncols, std::vector<int> mins, double *out) {
 // inequality multipliers 1, lam_e 0)
 kq_status init_state(kq_problem *h) {
   k_init_x<<<NB, NT, 0, h->stream>>>(h->P, h->S);
+  ++h->launches;
   if (h->m > 0) {
     kq_status rc = rowdot(h, h->S.x, h->t, h->tC);
     if (rc != KQ_OK) return rc;
   }
   k_init_rows<<<NB, NT, 0, h->stream>>>(h->P, h->S, h->t);
+  ++h->launches;
   KQ_CUDA(h, cudaGetLastError());
   h->kkt_valid = false;
   return KQ_OK;
@@ -626,14 +637,18 @@ static kq_status assemble_norms(kq_problem *h, double *norm2, double *rH2) {
   KQ_CUDA(h, cudaMemsetAsync(h->acc3, 0, P.n * sizeof(double), h->stream));
   KQ_CUDA(h, cudaMemsetAsync(h->red, 0, 4 * NB * sizeof(double), h->stream));
   k_rows_resid<<<NB, NT, 0, h->stream>>>(P, h->S, h->K, h->t, h->tC, cf, h->red + 2 * NB);
+  ++h->launches;
   if (P.hkind == KQ_H_CSR_LSQ) {
     k_csr_scatter<<<NB * 4, NT, 0, h->stream>>>(P, h->yP, cf, h->acc1, h->acc2, h->acc3);
+    ++h->launches;
     if (P.me > 0) return kq_fail(h, KQ_ERR_ARG, "CSR_LSQ with equality rows is not supported");
   } else if (P.m + P.me > 0) {
     if (P.adtype == KQ_F32) k_rows_scatter_dense<float><<<NB, NT, 0, h->stream>>>(P, cf, h->acc1, h->acc2, h->acc3);
     else k_rows_scatter_dense<double><<<NB, NT, 0, h->stream>>>(P, cf, h->acc1, h->acc2, h->acc3);
+    ++h->launches;
   }
   k_x_resid<<<NB, NT, 0, h->stream>>>(P, h->S, h->K, h->hx, h->acc1, h->acc2, h->acc3, h->red);
+  ++h->launches;
   KQ_CUDA(h, cudaGetLastError());
   double out[3];
   kq_status rc = fetch(h, 3, {0, 0, 0}, out);
@@ -665,6 +680,7 @@ void kq_default_ipm_opts(kq_ipm_opts *o) {
   o->inner_tol = 1e-4;
   o->timeout_s = 2.0;
   o->grid_ctas = 0;
+  o->verbose = 0;
 }
 
 void kq_default_pcg_opts(kq_pcg_opts *o) {
@@ -950,6 +966,7 @@ kq_status qp_set_state(kq_handle h, const double *x, const double *s_lA, const d
   for (auto &e : c)
     if (e.src && e.b) KQ_CUDA(h, cudaMemcpyAsync(e.dst, e.src, e.b, cudaMemcpyDefault, h->stream));
   k_set_state_mask<<<NB, NT, 0, h->stream>>>(h->P, h->S);
+  ++h->launches;
   KQ_CUDA(h, cudaGetLastError());
   KQ_CUDA(h, cudaStreamSynchronize(h->stream));
   h->mu = mu;
@@ -1020,6 +1037,7 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
                     kq_ipm_stats *stats) {
   if (!h) return kq_fail(nullptr, KQ_ERR_ARG, "null handle");
   auto t0 = std::chrono::steady_clock::now();
+  const long long launches0 = h->launches;
   kq_status rc0;
   kq_ipm_opts o;
   kq_default_ipm_opts(&o);
@@ -1052,6 +1070,7 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
     st.pcg_iters += ps.iters;
     st.pcg_kernel_ms += ps.kernel_ms;
     st.pcg_launches += 2 * ps.passes;
+    st.pcg_products += ps.iters + ps.passes;
     if (rc == KQ_WARN_PCG_MAXIT) st.pcg_maxit_hits++;
     else if (rc != KQ_OK) { final = rc; break; }
     // step recovery (A dx) and ratio test
@@ -1069,6 +1088,9 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
     const double rn = sqrt(n2);
     if (!(rn == rn)) { final = kq_fail(h, KQ_ERR_NUMERIC, "residual norm is NaN"); break; }
     st.res_norm = rn;
+    if (o.verbose)
+      fprintf(stderr, "ipm %3d mu %.0e |r| %.3e ax %.4f al %.4f pcg %5d passes %d rel %.2e %.2f ms\n",
+              it, mu, rn, ax, al, ps.iters, ps.passes, ps.rel_res, ps.kernel_ms);
     if (rn < mu) {
       if (mu < o.mu_tol) { final = KQ_OK; break; }
       ++kexp;
@@ -1106,6 +1128,7 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
   KQ_CUDA(h, cudaStreamSynchronize(h->stream));
   st.time_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   st.pcg_time_s = st.pcg_kernel_ms * 1e-3;
+  st.kernel_launches = h->launches - launches0;
   if (stats) *stats = st;
   if (final == KQ_ERR_IPM_MAXIT) kq_fail(h, final, "IPM iteration cap reached");
   return final;
@@ -1123,6 +1146,7 @@ kq_status qp_backward(kq_handle h, const double *gbar, double *grad_p, double *g
   if (rc != KQ_OK) return rc;
   KQ_CUDA(h, cudaMemcpyAsync(h->tmp, gbar, h->n * 8, cudaMemcpyDefault, h->stream));
   k_pad_rhs<<<NB, NT, 0, h->stream>>>(h->nkp, h->tmp, h->n, h->K.rhs);
+  ++h->launches;
   rc = pcg_solve(h, h->K.rhs, h->z, o, stats);
   h->kkt_valid = false;
   if (rc != KQ_OK && rc != KQ_WARN_PCG_MAXIT) return rc;

@@ -57,6 +57,47 @@ struct DevKKT {
   double mu;
 };
 
+// CSR staging tables.  A chunk is a run of consecutive rows of P whose
+// nonzeros (rounded out to 16-byte boundaries) fit one shared-memory stage.
+// Its descriptors are [header, one per row, sentinel]:
+//   header   {off = number of rows, a = 1 for a single over-long row, w2 = first row}
+//   row      {off = start of the row inside the staged chunk, a = A-row id or -1, w2}
+//   sentinel {off = end of the last row}
+struct RowDesc { int32_t off; int32_t a; double w2; };
+struct ChunkInfo { int64_t src; int32_t nelem; int32_t desc0; int32_t ndesc; int32_t pad; };
+constexpr int KQ_STAGES = 4;
+
+// Shared-memory layout of the staged CSR kernel (byte offsets), identical on
+// host (to size the launch) and device.
+struct CsrLayout {
+  size_t pw, acc, arho, acs, aDl, aDu, apl, apu, afl, tab, stage0, stage_bytes, val_off,
+      col_off, desc_off, bar, total;
+};
+__host__ __device__ inline size_t kq_up128(size_t x) { return (x + 127) & ~(size_t)127; }
+__host__ __device__ inline CsrLayout csr_layout(int win_cap, int a_cap, int ch_cap, int desc_cap,
+                                                int tab_cap) {
+  CsrLayout L;
+  size_t o = 0;
+  L.pw = o; o = kq_up128(o + 8 * (size_t)win_cap);
+  L.acc = o; o = kq_up128(o + 8 * (size_t)win_cap);
+  L.arho = o; o += 8 * (size_t)a_cap;
+  L.acs = o; o += 8 * (size_t)a_cap;
+  L.aDl = o; o += 8 * (size_t)a_cap;
+  L.aDu = o; o += 8 * (size_t)a_cap;
+  L.apl = o; o += 8 * (size_t)a_cap;
+  L.apu = o; o += 8 * (size_t)a_cap;
+  L.afl = o; o = kq_up128(o + (size_t)a_cap);
+  L.tab = o; o = kq_up128(o + sizeof(ChunkInfo) * (size_t)tab_cap);
+  L.val_off = 0;
+  L.col_off = kq_up128(4 * (size_t)ch_cap);
+  L.desc_off = L.col_off + kq_up128(4 * (size_t)ch_cap);
+  L.stage_bytes = L.desc_off + kq_up128(16 * (size_t)desc_cap);
+  L.stage0 = o; o += KQ_STAGES * L.stage_bytes;
+  L.bar = o; o += 8 * KQ_STAGES;
+  L.total = kq_up128(o);
+  return L;
+}
+
 // Work space of the persistent PCG kernels.
 struct PcgWork {
   int G = 0;                   // CTAs of the cooperative launch
@@ -73,6 +114,11 @@ struct PcgWork {
   int *err = nullptr;          // device error flag
   int *iters = nullptr;        // device iteration count
   double *resn = nullptr;      // device final recursive residual^2, bb
+  ChunkInfo *chunks = nullptr;
+  int32_t *cta_chunk = nullptr;
+  RowDesc *rdesc = nullptr;
+  int32_t *a_lo = nullptr, *a_hi = nullptr;
+  int a_cap = 0, ch_cap = 0, desc_cap = 0, tab_cap = 0;
   int64_t *row_begin = nullptr;   // G+1 partition of rows (P rows / dense rows)
   int32_t *win_lo = nullptr, *win_hi = nullptr;  // G column windows (CSR)
   int *h_pinned = nullptr;     // pinned host mirror for status words
@@ -107,6 +153,8 @@ struct kq_problem {
   bool solved = false;          // a converged ipm_solve ran
   int num_sms = 0;
   double timeout_s = 2.0;
+  long long launches = 0;       // kernels launched by this handle
+  long long pcg_launches = 0;   // persistent PCG launches (solve + apply)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
 

@@ -46,6 +46,12 @@ struct PcgArgs {
   int apply;
   int *iters;
   double *resn;
+  // CSR staging (bulk async copies of row chunks into shared memory)
+  const ChunkInfo *chunks;      // all chunks, CTA-major
+  const int32_t *cta_chunk;     // G+1 chunk ranges
+  const RowDesc *rdesc;         // row descriptors, chunk-major
+  const int32_t *a_lo, *a_hi;   // G ranges of A rows owned by each CTA's P rows
+  int a_cap, ch_cap, desc_cap, tab_cap;
 };
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
@@ -337,6 +343,289 @@ struct OpLowrank {
   }
 };
 
+// ---------------------------------------------------------------- CSR, staged through shared memory
+// The CTA's rows of P are cut into chunks (host, once per problem).  Thread 0
+// streams the chunks' values, columns and row descriptors into a ring of
+// KQ_STAGES shared-memory stages with 1-D bulk asynchronous copies completing
+// on an mbarrier per stage; the ring keeps running across PCG iterations (the
+// matrix does not change, only p), so the first chunks of the next product
+// are already in flight during the grid barriers.  Warps take one row each
+// from the staged chunk: dot with the p window, coefficient, scatter into
+// the shared accumulator.  Every mbarrier wait is bounded.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+struct PipeState {
+  uint32_t seq_issue = 0, seq_cons = 0;
+  int nc = 0, c0 = 0;
+};
+
+struct OpCsrStaged {
+  static __device__ __forceinline__ CsrLayout lay(const PcgArgs &a) {
+    return csr_layout(a.win_cap, a.a_cap, a.ch_cap, a.desc_cap, a.tab_cap);
+  }
+
+  // thread 0: start the copy of chunk number seq_issue (mod nc) into its stage
+  static __device__ void issue_chunk(const PcgArgs &a, unsigned char *smem, const CsrLayout &L,
+                                     const PipeState &ps) {
+    const int j = (int)(ps.seq_issue % (uint32_t)ps.nc);
+    const ChunkInfo ci = (j < a.tab_cap) ? reinterpret_cast<const ChunkInfo *>(smem + L.tab)[j]
+                                         : a.chunks[ps.c0 + j];
+    const int st = (int)(ps.seq_issue % KQ_STAGES);
+    unsigned char *sb = smem + L.stage0 + (size_t)st * L.stage_bytes;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar) + st;
+    const uint32_t bytes = (uint32_t)ci.ndesc * 16u + (ci.nelem > 0 ? (uint32_t)ci.nelem * 8u : 0u);
+    fence_proxy_async();
+    mbar_arrive_expect_tx(bar, bytes);
+    bulk_g2s(sb + L.desc_off, a.rdesc + ci.desc0, (uint32_t)ci.ndesc * 16u, bar);
+    if (ci.nelem > 0) {
+      bulk_g2s(sb + L.val_off, a.P.val + ci.src, (uint32_t)ci.nelem * 4u, bar);
+      bulk_g2s(sb + L.col_off, a.P.col + ci.src, (uint32_t)ci.nelem * 4u, bar);
+    }
+  }
+
+  // bounded wait for the copy of sequence number seq; false on timeout
+  static __device__ bool wait(const PcgArgs &a, unsigned char *smem, const CsrLayout &L,
+                              uint32_t seq) {
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar) + (seq % KQ_STAGES);
+    const uint32_t par = (seq / KQ_STAGES) & 1u;
+    if (mbar_try_wait(bar, par)) return true;
+    const uint64_t t0 = global_ns();
+    unsigned spins = 0;
+    while (!mbar_try_wait(bar, par)) {
+      if (((++spins) & 63u) == 0u && global_ns() - t0 > a.bar.budget_ns) return false;
+    }
+    return true;
+  }
+
+  static __device__ void begin(const PcgArgs &a, unsigned char *smem, PipeState &ps) {
+    const CsrLayout L = lay(a);
+    const int cta = blockIdx.x, tid = threadIdx.x;
+    ps.c0 = a.cta_chunk[cta];
+    ps.nc = a.cta_chunk[cta + 1] - ps.c0;
+    ps.seq_issue = ps.seq_cons = 0;
+    if (tid == 0) {
+      for (int s = 0; s < KQ_STAGES; ++s) mbar_init(reinterpret_cast<uint64_t *>(smem + L.bar) + s, 1);
+      fence_mbar_init();
+    }
+    ChunkInfo *tab = reinterpret_cast<ChunkInfo *>(smem + L.tab);
+    for (int j = tid; j < min(ps.nc, a.tab_cap); j += blockDim.x) tab[j] = a.chunks[ps.c0 + j];
+    const int alo = a.a_lo[cta], na = min(a.a_hi[cta] - alo, a.a_cap);
+    double *arho = reinterpret_cast<double *>(smem + L.arho);
+    double *acs = reinterpret_cast<double *>(smem + L.acs);
+    double *aDl = reinterpret_cast<double *>(smem + L.aDl);
+    double *aDu = reinterpret_cast<double *>(smem + L.aDu);
+    uint8_t *afl = smem + L.afl;
+    for (int i = tid; i < na; i += blockDim.x) {
+      const int ai = alo + i;
+      arho[i] = a.P.rhoA[ai];
+      acs[i] = a.cl[ai] + a.cu[ai];
+      aDl[i] = a.Dl[ai];
+      aDu[i] = a.Du[ai];
+      afl[i] = (uint8_t)((a.P.hasl[ai] ? 1 : 0) | (a.P.hasu[ai] ? 2 : 0));
+    }
+    __syncthreads();
+    if (ps.nc > 0) {
+      for (int s = 0; s < KQ_STAGES - 1; ++s) {
+        if (tid == 0) issue_chunk(a, smem, L, ps);
+        ps.seq_issue++;
+      }
+    }
+  }
+
+  // wait for every copy still in flight (bounded), so that the CTA never
+  // exits with asynchronous writes into its shared memory pending
+  static __device__ void drain(const PcgArgs &a, unsigned char *smem, PipeState &ps) {
+    const CsrLayout L = lay(a);
+    bool ok = true;
+    for (uint32_t s = ps.seq_cons; s < ps.seq_issue; ++s) ok = wait(a, smem, L, s) && ok;
+    if (!ok && threadIdx.x == 0) atomicCAS(a.bar.err, 0, 7);
+    __syncthreads();
+  }
+
+  template <class T>
+  static __device__ double phaseA(const PcgArgs &a, const double *ysrc, const double *pold,
+                                  double *pnew, double beta, int64_t vb, int64_t ve,
+                                  unsigned char *smem, PipeState &ps, bool &ok) {
+    const DevProb &P = a.P;
+    const CsrLayout L = lay(a);
+    const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    const int lo = a.win_lo[cta], hi = a.win_hi[cta];
+    const int wlen = hi - lo;
+    const bool win = wlen <= a.win_cap;
+    T *pw = reinterpret_cast<T *>(smem + L.pw);
+    T *acc = reinterpret_cast<T *>(smem + L.acc);
+    T *accg = reinterpret_cast<T *>(a.accx);
+    const int alo = a.a_lo[cta], na = min(a.a_hi[cta] - alo, a.a_cap);
+    const double *arho = reinterpret_cast<const double *>(smem + L.arho);
+    const double *acs = reinterpret_cast<const double *>(smem + L.acs);
+    const double *aDl = reinterpret_cast<const double *>(smem + L.aDl);
+    const double *aDu = reinterpret_cast<const double *>(smem + L.aDu);
+    double *apl = reinterpret_cast<double *>(smem + L.apl);
+    double *apu = reinterpret_cast<double *>(smem + L.apu);
+    const uint8_t *afl = smem + L.afl;
+    const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
+    double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
+    if (win) {
+      for (int j = tid; j < wlen; j += blockDim.x) {
+        const int c = lo + j;
+        pw[j] = (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+        acc[j] = (T)0;
+      }
+    }
+    for (int i = tid; i < na; i += blockDim.x) {
+      const int ai = alo + i;
+      apl[i] = (afl[i] & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
+      apu[i] = (afl[i] & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
+    }
+    __syncthreads();
+    __shared__ double s_bcast[2];
+    for (int j = 0; j < ps.nc; ++j) {
+      if (tid == 0) issue_chunk(a, smem, L, ps);
+      ps.seq_issue++;
+      const bool w = wait(a, smem, L, ps.seq_cons);
+      if (__syncthreads_or(!w)) {
+        if (tid == 0) atomicCAS(a.bar.err, 0, 7);
+        ok = false;
+        return 0.0;
+      }
+      const int st = (int)(ps.seq_cons % KQ_STAGES);
+      const unsigned char *sb = smem + L.stage0 + (size_t)st * L.stage_bytes;
+      const float *sval = reinterpret_cast<const float *>(sb + L.val_off);
+      const int *scol = reinterpret_cast<const int *>(sb + L.col_off);
+      const RowDesc *sd = reinterpret_cast<const RowDesc *>(sb + L.desc_off);
+      const int nrows = sd[0].off;
+      if (sd[0].a == 0) {
+        for (int i = warp; i < nrows; i += nw) {
+          const RowDesc d = sd[1 + i];
+          const int end = sd[2 + i].off;
+          T dot = (T)0;
+          for (int k = d.off + lane; k < end; k += 32) {
+            const int c = scol[k];
+            const T pv = win ? pw[c - lo] : (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+            dot += (T)sval[k] * pv;
+          }
+          dot = warp_sum(dot);
+          const double dd = (double)dot;
+          double ud = d.w2 * dd;
+          if (d.a >= 0) {
+            const int ai = d.a, il = ai - alo;
+            double rho, cs, Dl, Du, pl, pu;
+            int fl;
+            if (il >= 0 && il < na) {
+              rho = arho[il]; cs = acs[il]; Dl = aDl[il]; Du = aDu[il]; fl = afl[il];
+              pl = apl[il]; pu = apu[il];
+            } else {
+              rho = P.rhoA[ai]; cs = a.cl[ai] + a.cu[ai]; Dl = a.Dl[ai]; Du = a.Du[ai];
+              fl = (P.hasl[ai] ? 1 : 0) | (P.hasu[ai] ? 2 : 0);
+              pl = (fl & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
+              pu = (fl & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
+            }
+            const double t = rho * dd;
+            const double coef = 2.0 * t * cs + pl - pu;
+            ud += rho * coef;
+            if (lane == 0) {
+              const double ql = (fl & 1) ? t + Dl * pl : 0.0;
+              const double qu = (fl & 2) ? -t + Du * pu : 0.0;
+              a.qlam[P.me + ai] = ql;
+              a.qlam[P.me + P.m + ai] = qu;
+              pq += pl * ql + pu * qu;
+            }
+          }
+          if (lane == 0) pq += ud * dd;
+          const T u = (T)ud;
+          for (int k = d.off + lane; k < end; k += 32) {
+            const int c = scol[k];
+            if (win) atomicAdd(acc + (c - lo), u * (T)sval[k]);
+            else atomicAdd(accg + c, u * (T)sval[k]);
+          }
+        }
+      } else {
+        // a single row longer than a stage: whole CTA, straight from global memory
+        const int64_t r = (int64_t)sd[0].w2;
+        const RowDesc d = sd[1];
+        const int64_t s = P.rowptr[r], e = P.rowptr[r + 1];
+        double part[1] = {0.0};
+        for (int64_t k = s + tid; k < e; k += blockDim.x) {
+          const int c = P.col[k];
+          const T pv = win ? pw[c - lo] : (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+          part[0] += (double)((T)P.val[k] * pv);
+        }
+        __shared__ double shl[32];
+        block_sum<1>(part, shl);
+        if (tid == 0) {
+          const double dd = part[0];
+          double ud = d.w2 * dd;
+          if (d.a >= 0) {
+            const int ai = d.a;
+            const double rho = P.rhoA[ai];
+            const int fl = (P.hasl[ai] ? 1 : 0) | (P.hasu[ai] ? 2 : 0);
+            const double pl = (fl & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
+            const double pu = (fl & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
+            const double t = rho * dd;
+            const double coef = 2.0 * t * (a.cl[ai] + a.cu[ai]) + pl - pu;
+            ud += rho * coef;
+            const double ql = (fl & 1) ? t + a.Dl[ai] * pl : 0.0;
+            const double qu = (fl & 2) ? -t + a.Du[ai] * pu : 0.0;
+            a.qlam[P.me + ai] = ql;
+            a.qlam[P.me + P.m + ai] = qu;
+            pq += pl * ql + pu * qu;
+          }
+          pq += ud * dd;
+          s_bcast[0] = ud;
+        }
+        __syncthreads();
+        const T u = (T)s_bcast[0];
+        for (int64_t k = s + tid; k < e; k += blockDim.x) {
+          const int c = P.col[k];
+          if (win) atomicAdd(acc + (c - lo), u * (T)P.val[k]);
+          else atomicAdd(accg + c, u * (T)P.val[k]);
+        }
+      }
+      __syncthreads();
+      ps.seq_cons++;
+    }
+    if (win) {
+      for (int j = tid; j < wlen; j += blockDim.x) {
+        const T v = acc[j];
+        if (v != (T)0) atomicAdd(accg + lo + j, v);
+      }
+    }
+    return pq;
+  }
+};
+
+template <class OP> struct IsStaged { static constexpr bool value = false; };
+template <> struct IsStaged<OpCsrStaged> { static constexpr bool value = true; };
+
 template <class OP> struct IsLowrank { static constexpr bool value = false; };
 template <class ZS> struct IsLowrank<OpLowrank<ZS>> { static constexpr bool value = true; };
 
@@ -344,9 +633,12 @@ template <class OP, class T>
 __device__ __forceinline__ double run_phaseA(const PcgArgs &a, const double *ysrc,
                                              const double *pold, double *pnew, double beta,
                                              int64_t vb, int64_t ve, unsigned char *smem,
-                                             bool &ok) {
+                                             PipeState &ps, bool &ok) {
   if constexpr (IsLowrank<OP>::value) {
     return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ok);
+  } else if constexpr (IsStaged<OP>::value) {
+    ok = true;
+    return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ps, ok);
   } else {
     ok = true;
     return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem);
@@ -367,6 +659,8 @@ __global__ void __launch_bounds__(512, 1) pcg_kernel(PcgArgs a) {
   int it = 0;
   bool ok = true;
   const double *ysrc = a.apply ? a.rhs : a.y;
+  PipeState ps;
+  if constexpr (IsStaged<OP>::value) OP::begin(a, smem, ps);
 
   // ---- initialisation: z = 0, r = rhs, y = r / diag, p_old = 0
   {
@@ -398,7 +692,7 @@ __global__ void __launch_bounds__(512, 1) pcg_kernel(PcgArgs a) {
   while (ok) {
     if (!a.apply && (rr <= a.tol2 * bb || it >= a.maxit)) break;
     // ---- phase A: q = K p,  p = y + beta p_old
-    double pq = run_phaseA<OP, T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ok);
+    double pq = run_phaseA<OP, T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ps, ok);
     if (!ok) break;
     {
       double v1[1] = {pq};
@@ -452,6 +746,7 @@ __global__ void __launch_bounds__(512, 1) pcg_kernel(PcgArgs a) {
     double *t = pold; pold = pnew; pnew = t;
     ++it;
   }
+  if constexpr (IsStaged<OP>::value) OP::drain(a, smem, ps);
   if (cta == 0 && tid == 0) {
     *a.iters = it;
     a.resn[0] = rr;
@@ -520,7 +815,7 @@ __global__ void k_final_sum(int nb, const double *part, double *out) {
 using KFun = void (*)(PcgArgs);
 
 template <class T> KFun pick_kernel(const DevProb &P) {
-  if (P.hkind == KQ_H_CSR_LSQ) return pcg_kernel<OpCsr, T>;
+  if (P.hkind == KQ_H_CSR_LSQ) return pcg_kernel<OpCsrStaged, T>;
   if (P.hkind == KQ_H_LOWRANK) {
     if (P.hdtype == KQ_F64) return pcg_kernel<OpLowrank<double>, T>;
     return pcg_kernel<OpLowrank<float>, T>;
@@ -558,6 +853,9 @@ kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double t
   a.bar.budget_ns = (uint64_t)(h->timeout_s * 1e9);
   a.tol2 = tol * tol; a.maxit = maxit; a.apply = apply;
   a.iters = W.iters; a.resn = W.resn;
+  a.chunks = W.chunks; a.cta_chunk = W.cta_chunk; a.rdesc = W.rdesc;
+  a.a_lo = W.a_lo; a.a_hi = W.a_hi;
+  a.a_cap = W.a_cap; a.ch_cap = W.ch_cap; a.desc_cap = W.desc_cap; a.tab_cap = W.tab_cap;
   KFun f = prec == KQ_PREC_MIXED ? pick_kernel<float>(h->P) : pick_kernel<double>(h->P);
   KQ_CUDA(h, cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)W.smem));
@@ -567,6 +865,8 @@ kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double t
   KQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
   KQ_CUDA(h, cudaLaunchCooperativeKernel((const void *)f, dim3(W.G), dim3(W.threads), args,
                                          W.smem, h->stream));
+  ++h->launches;
+  ++h->pcg_launches;
   KQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
   // status words back to the host
   KQ_CUDA(h, cudaMemcpyAsync(W.h_pinned, W.err, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
@@ -590,7 +890,9 @@ kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double t
 double dev_norm(kq_problem *h, const double *v, int64_t N) {
   const int nb = 256;
   k_sumsq<<<nb, 256, 0, h->stream>>>(N, v, h->red);
+  ++h->launches;
   k_final_sum<<<1, 256, 0, h->stream>>>(nb, h->red, h->red_out);
+  ++h->launches;
   cudaMemcpyAsync(h->h_red, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   cudaStreamSynchronize(h->stream);
   return sqrt(h->h_red[0]);
@@ -628,8 +930,9 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
   W.win_hi = dalloc<int32_t>(h, G);
   if (!W.row_begin || !W.win_lo || !W.win_hi) return kq_fail(h, KQ_ERR_OOM, "pcg partition");
   std::vector<int64_t> rb(G + 1, 0);
+  std::vector<int64_t> rp;
   if (P.hkind == KQ_H_CSR_LSQ) {
-    std::vector<int64_t> rp(P.nP + 1);
+    rp.resize(P.nP + 1);
     KQ_CUDA(h, cudaMemcpy(rp.data(), P.rowptr, (P.nP + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost));
     const int64_t nnz = rp[P.nP];
     for (int c = 0; c <= G; ++c) {
@@ -647,6 +950,7 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
   KQ_CUDA(h, cudaMemcpy(W.row_begin, rb.data(), (G + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
   if (P.hkind == KQ_H_CSR_LSQ) {
     k_windows<<<G, 256, 0, h->stream>>>(P.rowptr, P.col, W.row_begin, W.win_lo, W.win_hi);
+    ++h->launches;
     KQ_CUDA(h, cudaGetLastError());
     std::vector<int32_t> lo(G), hi(G);
     KQ_CUDA(h, cudaMemcpyAsync(lo.data(), W.win_lo, G * 4, cudaMemcpyDeviceToHost, h->stream));
@@ -654,9 +958,82 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
     KQ_CUDA(h, cudaStreamSynchronize(h->stream));
     int wmax = 0;
     for (int c = 0; c < G; ++c) wmax = std::max(wmax, hi[c] - lo[c]);
-    const int cap_elems = (int)(160 * 1024 / (2 * sizeof(double)));
-    win_cap = std::min(wmax, cap_elems);
-    smem = (size_t)2 * win_cap * sizeof(double);
+    // ---- chunk tables for the staged kernel
+    const int ch_cap = 4096;             // values (and columns) per stage
+    const int desc_cap = 128;            // descriptors per stage
+    std::vector<int32_t> p2a(P.nP);
+    std::vector<double> w2(P.nP);
+    KQ_CUDA(h, cudaMemcpy(p2a.data(), P.prow2a, P.nP * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    KQ_CUDA(h, cudaMemcpy(w2.data(), P.w2, P.nP * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<ChunkInfo> chunks;
+    std::vector<RowDesc> desc;
+    std::vector<int32_t> cta_chunk(G + 1, 0), alo(G, 0), ahi(G, 0);
+    int max_nc = 0, a_max = 0;
+    for (int c = 0; c < G; ++c) {
+      cta_chunk[c] = (int32_t)chunks.size();
+      int amin = INT32_MAX, amax = -1;
+      int64_t r = rb[c];
+      while (r < rb[c + 1]) {
+        ChunkInfo ci{};
+        ci.desc0 = (int32_t)desc.size();
+        const int64_t s0 = rp[r];
+        const int64_t s_al = s0 & ~(int64_t)3;   // 16-byte aligned start
+        if (rp[r + 1] - s_al + 4 > ch_cap) {
+          // over-long row: processed from global memory by the whole CTA
+          desc.push_back(RowDesc{1, 1, (double)r});
+          desc.push_back(RowDesc{0, p2a[r], w2[r]});
+          desc.push_back(RowDesc{0, 0, 0.0});
+          ci.src = 0;
+          ci.nelem = 0;
+          if (p2a[r] >= 0) { amin = std::min(amin, p2a[r]); amax = std::max(amax, p2a[r]); }
+          ++r;
+        } else {
+          desc.push_back(RowDesc{0, 0, (double)r});
+          int nr = 0;
+          while (r < rb[c + 1] && nr < desc_cap - 2 && rp[r + 1] - s_al + 4 <= ch_cap) {
+            desc.push_back(RowDesc{(int32_t)(rp[r] - s_al), p2a[r], w2[r]});
+            if (p2a[r] >= 0) { amin = std::min(amin, p2a[r]); amax = std::max(amax, p2a[r]); }
+            ++nr;
+            ++r;
+          }
+          const int64_t e = rp[r];
+          desc.push_back(RowDesc{(int32_t)(e - s_al), 0, 0.0});
+          desc[ci.desc0].off = nr;
+          ci.src = s_al;
+          ci.nelem = (int32_t)(((e - s_al) + 3) & ~(int64_t)3);
+        }
+        ci.ndesc = (int32_t)desc.size() - ci.desc0;
+        // keep every chunk's descriptor block 16-byte aligned (RowDesc is 16 B)
+        chunks.push_back(ci);
+      }
+      max_nc = std::max(max_nc, (int)chunks.size() - cta_chunk[c]);
+      alo[c] = amax >= 0 ? amin : 0;
+      ahi[c] = amax >= 0 ? amax + 1 : 0;
+      a_max = std::max(a_max, ahi[c] - alo[c]);
+    }
+    cta_chunk[G] = (int32_t)chunks.size();
+    W.ch_cap = ch_cap;
+    W.desc_cap = desc_cap;
+    W.tab_cap = std::min(max_nc, 512);
+    W.a_cap = std::min(a_max, 1024);
+    // shared memory: window + A rows + chunk table + stages; shrink the window if needed
+    const size_t limit = 220 * 1024;
+    win_cap = wmax;
+    while (csr_layout(win_cap, W.a_cap, ch_cap, desc_cap, W.tab_cap).total > limit && win_cap > 0)
+      win_cap = win_cap > 1024 ? win_cap - 1024 : 0;
+    smem = csr_layout(win_cap, W.a_cap, ch_cap, desc_cap, W.tab_cap).total;
+    W.chunks = dalloc<ChunkInfo>(h, chunks.size());
+    W.rdesc = dalloc<RowDesc>(h, desc.size());
+    W.cta_chunk = dalloc<int32_t>(h, G + 1);
+    W.a_lo = dalloc<int32_t>(h, G);
+    W.a_hi = dalloc<int32_t>(h, G);
+    if (!W.chunks || !W.rdesc || !W.cta_chunk || !W.a_lo || !W.a_hi)
+      return kq_fail(h, KQ_ERR_OOM, "chunk tables");
+    KQ_CUDA(h, cudaMemcpy(W.chunks, chunks.data(), chunks.size() * sizeof(ChunkInfo), cudaMemcpyHostToDevice));
+    KQ_CUDA(h, cudaMemcpy(W.rdesc, desc.data(), desc.size() * sizeof(RowDesc), cudaMemcpyHostToDevice));
+    KQ_CUDA(h, cudaMemcpy(W.cta_chunk, cta_chunk.data(), (G + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
+    KQ_CUDA(h, cudaMemcpy(W.a_lo, alo.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice));
+    KQ_CUDA(h, cudaMemcpy(W.a_hi, ahi.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice));
   } else if (P.hkind == KQ_H_LOWRANK) {
     int64_t rmax = 0;
     for (int c = 0; c < G; ++c) rmax = std::max(rmax, rb[c + 1] - rb[c]);
@@ -747,13 +1124,16 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
     s.passes++;
     if (rc != KQ_OK) break;
     k_add<<<256, 256, 0, h->stream>>>(N, z, dz);
+    ++h->launches;
     float ms = 0.f;
     rc = pcg_apply(h, z, dz, KQ_PREC_F64, &ms);
     s.kernel_ms += ms;
     if (rc != KQ_OK) break;
     const int nb = 256;
     k_axpy_res<<<nb, 256, 0, h->stream>>>(N, rhs, dz, res, h->red);
+    ++h->launches;
     k_final_sum<<<1, 256, 0, h->stream>>>(nb, h->red, h->red_out);
+    ++h->launches;
     KQ_CUDA(h, cudaMemcpyAsync(h->h_red, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
     KQ_CUDA(h, cudaStreamSynchronize(h->stream));
     resn = sqrt(h->h_red[0]);

@@ -187,7 +187,10 @@ def _banded_csr_pattern(rng, rows, cols, nnz_row, halfwin, chunk=4096):
 
 
 def dose_qp(rows: int = 200_000, cols: int = 20_000, nnz_row: int = 100,
-            halfwin: int = 1000, ntarget: int = 10_000, seed: int = 1) -> QPData:
+            halfwin: int = 1000, ntarget: int = 10_000, seed: int = 1,
+            unit_dose: bool = False) -> QPData:
+    """``unit_dose``: the reference plan is rescaled so that its mean target
+    dose is 1, the units of d ~ U(0,1) (prescription dose 1)."""
     rng = np.random.default_rng(seed)
     assert nnz_row <= halfwin + 1, "window too narrow for nnz_row"
     indptr, indices = _banded_csr_pattern(rng, rows, cols, nnz_row, halfwin)
@@ -198,6 +201,8 @@ def dose_qp(rows: int = 200_000, cols: int = 20_000, nnz_row: int = 100,
     T = np.sort(rng.permutation(rows)[:ntarget]).astype(np.int32)
     xhat = rng.uniform(0.5, 1.5, cols)
     P64 = P.astype(np.float64)
+    if unit_dose:
+        xhat = xhat / float(np.mean(P64[T] @ xhat))
     p = -2.0 * (P64.T @ (w * d))
     dose_hat = P64[T] @ xhat
     return QPData(n=cols, hkind="csr_lsq", p=p, P=P, w=w, akind="rows_of_p",
@@ -207,14 +212,46 @@ def dose_qp(rows: int = 200_000, cols: int = 20_000, nnz_row: int = 100,
                         "halfwin": halfwin, "d": d, "xhat": xhat})
 
 
+def irregular_lsq_qp(rows: int = 3000, cols: int = 5000, max_len: int = 250,
+                     long_rows: int = 2, long_len: int = 4500, ntarget: int = 300,
+                     seed: int = 12) -> QPData:
+    """Least-squares QP with an irregular P: row lengths U{0..max_len} with
+    uniformly scattered columns, plus a few over-long rows; two-sided limits
+    on ntarget rows around a feasible reference plan; 0 <= x <= 2."""
+    rng = np.random.default_rng(seed)
+    lens = np.floor(rng.random(rows) * (max_len + 1)).astype(np.int64)
+    pos = np.sort(rng.permutation(rows)[:long_rows])
+    lens[pos] = long_len
+    indptr = np.concatenate([[0], np.cumsum(lens)]).astype(np.int64)
+    indices = np.empty(indptr[-1], dtype=np.int32)
+    for r in range(rows):
+        keys = rng.random(cols)
+        indices[indptr[r]:indptr[r + 1]] = np.sort(np.argpartition(keys, lens[r])[:lens[r]]) \
+            if lens[r] < cols else np.arange(cols)
+    vals = rng.lognormal(0.0, 1.0, indptr[-1]).astype(np.float32)
+    P = sp.csr_matrix((vals, indices, indptr), shape=(rows, cols))
+    w = rng.uniform(0.5, 2.0, rows)
+    d = rng.uniform(0.0, 1.0, rows)
+    nz = np.nonzero(lens > 0)[0]
+    T = np.sort(nz[rng.permutation(len(nz))[:ntarget]]).astype(np.int32)
+    xhat = rng.uniform(0.5, 1.5, cols)
+    P64 = P.astype(np.float64)
+    xhat = xhat / float(np.mean(P64[T] @ xhat))
+    p = -2.0 * (P64.T @ (w * d))
+    dose_hat = P64[T] @ xhat
+    return QPData(n=cols, hkind="csr_lsq", p=p, P=P, w=w, akind="rows_of_p", a_rows=T,
+                  lA=0.9 * dose_hat, uA=1.1 * dose_hat, lx=_full(cols, 0.0),
+                  ux=_full(cols, 2.0 * float(np.max(xhat))), meta={"seed": seed})
+
+
 def config1() -> QPData:
     """Dose-shaped QP: P 200k x 20k, 2e7 nnz, 10k target rows, seed 1."""
-    return dose_qp(200_000, 20_000, 100, 1000, 10_000, seed=1)
+    return dose_qp(200_000, 20_000, 100, 1000, 10_000, seed=1, unit_dose=True)
 
 
 def config4() -> QPData:
     """Dose-shaped QP at 1/4 size: P 50k x 5k, 5e6 nnz, 2.5k targets, seed 4."""
-    return dose_qp(50_000, 5_000, 100, 1000, 2_500, seed=4)
+    return dose_qp(50_000, 5_000, 100, 1000, 2_500, seed=4, unit_dose=True)
 
 
 def config4_directions(qp: QPData, ndir: int = 32, seed: int = 4):

@@ -24,6 +24,9 @@ PROBLEMS = {
     "dense_eq": lambda: qpgen.tiny_qp(37, 23, 5, me=2),
     "dense_onesided": lambda: qpgen.dense_qp(70, 45, seed=3),
     "csr": lambda: qpgen.dose_qp(3000, 300, 30, 40, 150, seed=8),
+    "csr_multichunk": lambda: qpgen.dose_qp(60000, 3000, 100, 300, 3000, seed=10,
+                                            unit_dose=True),
+    "csr_irregular": lambda: qpgen.irregular_lsq_qp(),
     "lowrank": lambda: qpgen.svm_qp(500, 16, seed=9),
 }
 
@@ -123,11 +126,20 @@ def test_kkt_pcg_solve(kq, name, prec):
     assert relerr(z, zs) <= 1e-6
 
 
+_ORACLE = {}
+
+
+def _oracle_result(name):
+    if name not in _ORACLE:
+        _ORACLE[name] = oracle.ipm_solve(PROBLEMS[name]())
+    return _ORACLE[name]
+
+
 @pytest.mark.parametrize("prec", [0, 1], ids=["f64", "mixed"])
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_ipm_matches_oracle(kq, name, prec):
     qp = PROBLEMS[name]()
-    res = oracle.ipm_solve(qp)
+    res = _oracle_result(name)
     assert res.status == "converged"
     opts = kq.default_ipm_opts(precision=prec)
     rc, st, out = kq.solve(qp, opts)
