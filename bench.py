@@ -238,10 +238,17 @@ def main():
         kq.qp_residuals(h, rhs=rhs)
         po = kq.default_pcg_opts(tol=1e-30, maxit=args.pcg_iters, precision=prec,
                                  refine_steps=1 if prec else 0, inner_tol=1e-30)
+        res = []
         for _ in range(max(1, args.steps)):
-            kq.kkt_pcg_solve(h, rhs, sol, po)
+            rc, st = kq.kkt_pcg_solve(h, rhs, sol, po)
+            res.append(st.as_dict())
         torch.cuda.synchronize()
-        print(json.dumps({"mode": "pcg", "iters": args.pcg_iters}))
+        last = res[-1]
+        us = 1e3 * last["kernel_ms"] / max(1, last["iters"] + last["passes"])
+        print(json.dumps({"mode": "pcg", "iters": last["iters"], "kernel_ms": last["kernel_ms"],
+                          "us_per_product": us, "kv_gbs": algo_bytes(qp) / (us * 1e-6) / 1e9,
+                          "env": {k: os.environ.get(k) for k in ("KQ_CHUNK", "KQ_STAGES",
+                                                                 "KQ_COPY_PIECE")}}))
         return 0
 
     def solve():

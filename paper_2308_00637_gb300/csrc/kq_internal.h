@@ -60,12 +60,15 @@ struct DevKKT {
 // CSR staging tables.  A chunk is a run of consecutive rows of P whose
 // nonzeros (rounded out to 16-byte boundaries) fit one shared-memory stage.
 // Its descriptors are [header, one per row, sentinel]:
-//   header   {off = number of rows, a = 1 for a single over-long row, w2 = first row}
-//   row      {off = start of the row inside the staged chunk, a = A-row id or -1, w2}
+//   header   {off = number of rows, a = -1, or the row index of a single
+//             over-long row that is read from global memory}
+//   row      {off = start of the row inside the staged chunk, a = A-row id or -1,
+//             w2 = 2 sigma w_r as an FP32 pair hi + lo (hi alone in FP32
+//             products; hi + lo, 48 significant bits, in FP64 products)}
 //   sentinel {off = end of the last row}
-struct RowDesc { int32_t off; int32_t a; double w2; };
+struct RowDesc { int32_t off; int32_t a; float w2hi; float w2lo; };
 struct ChunkInfo { int64_t src; int32_t nelem; int32_t desc0; int32_t ndesc; int32_t pad; };
-constexpr int KQ_STAGES = 4;
+constexpr int KQ_MAX_STAGES = 8;
 
 // Shared-memory layout of the staged CSR kernel (byte offsets), identical on
 // host (to size the launch) and device.
@@ -75,7 +78,7 @@ struct CsrLayout {
 };
 __host__ __device__ inline size_t kq_up128(size_t x) { return (x + 127) & ~(size_t)127; }
 __host__ __device__ inline CsrLayout csr_layout(int win_cap, int a_cap, int ch_cap, int desc_cap,
-                                                int tab_cap) {
+                                                int tab_cap, int stages) {
   CsrLayout L;
   size_t o = 0;
   L.pw = o; o = kq_up128(o + 8 * (size_t)win_cap);
@@ -92,8 +95,8 @@ __host__ __device__ inline CsrLayout csr_layout(int win_cap, int a_cap, int ch_c
   L.col_off = kq_up128(4 * (size_t)ch_cap);
   L.desc_off = L.col_off + kq_up128(4 * (size_t)ch_cap);
   L.stage_bytes = L.desc_off + kq_up128(16 * (size_t)desc_cap);
-  L.stage0 = o; o += KQ_STAGES * L.stage_bytes;
-  L.bar = o; o += 8 * KQ_STAGES;
+  L.stage0 = o; o += (size_t)stages * L.stage_bytes;
+  L.bar = o; o += 8 * (size_t)stages;
   L.total = kq_up128(o);
   return L;
 }
@@ -119,6 +122,7 @@ struct PcgWork {
   RowDesc *rdesc = nullptr;
   int32_t *a_lo = nullptr, *a_hi = nullptr;
   int a_cap = 0, ch_cap = 0, desc_cap = 0, tab_cap = 0;
+  int stages = 4, copy_piece = 16384, producer = 0;
   int64_t *row_begin = nullptr;   // G+1 partition of rows (P rows / dense rows)
   int32_t *win_lo = nullptr, *win_hi = nullptr;  // G column windows (CSR)
   int *h_pinned = nullptr;     // pinned host mirror for status words

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "kq_internal.h"
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 namespace {
@@ -52,6 +53,9 @@ struct PcgArgs {
   const RowDesc *rdesc;         // row descriptors, chunk-major
   const int32_t *a_lo, *a_hi;   // G ranges of A rows owned by each CTA's P rows
   int a_cap, ch_cap, desc_cap, tab_cap;
+  int copy_piece;               // bytes per bulk copy (multiple of 16)
+  int stages;                   // shared-memory ring depth
+  int producer;                 // 0: per-thread cp.async, 1: bulk copies + mbarrier
 };
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
@@ -346,7 +350,7 @@ struct OpLowrank {
 // ---------------------------------------------------------------- CSR, staged through shared memory
 // The CTA's rows of P are cut into chunks (host, once per problem).  Thread 0
 // streams the chunks' values, columns and row descriptors into a ring of
-// KQ_STAGES shared-memory stages with 1-D bulk asynchronous copies completing
+// `stages` shared-memory stages with 1-D bulk asynchronous copies completing
 // on an mbarrier per stage; the ring keeps running across PCG iterations (the
 // matrix does not change, only p), so the first chunks of the next product
 // are already in flight during the grid barriers.  Warps take one row each
@@ -382,6 +386,24 @@ __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
+// per-thread 16-byte asynchronous copies (LSU path), grouped per chunk
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_pending(int n) {
+  switch (n) {
+    case 0: asm volatile("cp.async.wait_group 0;" ::: "memory"); break;
+    case 1: asm volatile("cp.async.wait_group 1;" ::: "memory"); break;
+    case 2: asm volatile("cp.async.wait_group 2;" ::: "memory"); break;
+    case 3: asm volatile("cp.async.wait_group 3;" ::: "memory"); break;
+    case 4: asm volatile("cp.async.wait_group 4;" ::: "memory"); break;
+    case 5: asm volatile("cp.async.wait_group 5;" ::: "memory"); break;
+    case 6: asm volatile("cp.async.wait_group 6;" ::: "memory"); break;
+    default: asm volatile("cp.async.wait_group 7;" ::: "memory"); break;
+  }
+}
+
 struct PipeState {
   uint32_t seq_issue = 0, seq_cons = 0;
   int nc = 0, c0 = 0;
@@ -389,7 +411,7 @@ struct PipeState {
 
 struct OpCsrStaged {
   static __device__ __forceinline__ CsrLayout lay(const PcgArgs &a) {
-    return csr_layout(a.win_cap, a.a_cap, a.ch_cap, a.desc_cap, a.tab_cap);
+    return csr_layout(a.win_cap, a.a_cap, a.ch_cap, a.desc_cap, a.tab_cap, a.stages);
   }
 
   // thread 0: start the copy of chunk number seq_issue (mod nc) into its stage
@@ -398,7 +420,7 @@ struct OpCsrStaged {
     const int j = (int)(ps.seq_issue % (uint32_t)ps.nc);
     const ChunkInfo ci = (j < a.tab_cap) ? reinterpret_cast<const ChunkInfo *>(smem + L.tab)[j]
                                          : a.chunks[ps.c0 + j];
-    const int st = (int)(ps.seq_issue % KQ_STAGES);
+    const int st = (int)(ps.seq_issue % (uint32_t)a.stages);
     unsigned char *sb = smem + L.stage0 + (size_t)st * L.stage_bytes;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar) + st;
     const uint32_t bytes = (uint32_t)ci.ndesc * 16u + (ci.nelem > 0 ? (uint32_t)ci.nelem * 8u : 0u);
@@ -406,16 +428,44 @@ struct OpCsrStaged {
     mbar_arrive_expect_tx(bar, bytes);
     bulk_g2s(sb + L.desc_off, a.rdesc + ci.desc0, (uint32_t)ci.ndesc * 16u, bar);
     if (ci.nelem > 0) {
-      bulk_g2s(sb + L.val_off, a.P.val + ci.src, (uint32_t)ci.nelem * 4u, bar);
-      bulk_g2s(sb + L.col_off, a.P.col + ci.src, (uint32_t)ci.nelem * 4u, bar);
+      // split into pieces of copy_piece bytes (a multiple of 16): several
+      // smaller copies keep more requests in flight than one large one
+      const uint32_t total = (uint32_t)ci.nelem * 4u, piece = (uint32_t)a.copy_piece;
+      for (uint32_t o = 0; o < total; o += piece) {
+        const uint32_t nb = min(piece, total - o);
+        bulk_g2s(sb + L.val_off + o, reinterpret_cast<const unsigned char *>(a.P.val + ci.src) + o, nb, bar);
+        bulk_g2s(sb + L.col_off + o, reinterpret_cast<const unsigned char *>(a.P.col + ci.src) + o, nb, bar);
+      }
     }
+  }
+
+  // all threads: copy chunk number seq_issue (mod nc) into its stage with
+  // 16-byte cp.async pieces, one commit group per chunk
+  static __device__ void issue_chunk_lsu(const PcgArgs &a, unsigned char *smem, const CsrLayout &L,
+                                         const PipeState &ps) {
+    const int j = (int)(ps.seq_issue % (uint32_t)ps.nc);
+    const ChunkInfo ci = (j < a.tab_cap) ? reinterpret_cast<const ChunkInfo *>(smem + L.tab)[j]
+                                         : a.chunks[ps.c0 + j];
+    const int st = (int)(ps.seq_issue % (uint32_t)a.stages);
+    unsigned char *sb = smem + L.stage0 + (size_t)st * L.stage_bytes;
+    const int nv = ci.nelem > 0 ? ci.nelem >> 2 : 0;   // 16-byte pieces of val (and of col)
+    const int nd = ci.ndesc;                            // 16-byte descriptors
+    const float4 *gv = reinterpret_cast<const float4 *>(a.P.val + ci.src);
+    const int4 *gc = reinterpret_cast<const int4 *>(a.P.col + ci.src);
+    const int4 *gd = reinterpret_cast<const int4 *>(a.rdesc + ci.desc0);
+    for (int q = threadIdx.x; q < nv; q += blockDim.x) {
+      cp_async16(sb + L.val_off + 16 * (size_t)q, gv + q);
+      cp_async16(sb + L.col_off + 16 * (size_t)q, gc + q);
+    }
+    for (int q = threadIdx.x; q < nd; q += blockDim.x) cp_async16(sb + L.desc_off + 16 * (size_t)q, gd + q);
+    cp_async_commit();
   }
 
   // bounded wait for the copy of sequence number seq; false on timeout
   static __device__ bool wait(const PcgArgs &a, unsigned char *smem, const CsrLayout &L,
                               uint32_t seq) {
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar) + (seq % KQ_STAGES);
-    const uint32_t par = (seq / KQ_STAGES) & 1u;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + L.bar) + (seq % (uint32_t)a.stages);
+    const uint32_t par = (seq / (uint32_t)a.stages) & 1u;
     if (mbar_try_wait(bar, par)) return true;
     const uint64_t t0 = global_ns();
     unsigned spins = 0;
@@ -425,6 +475,7 @@ struct OpCsrStaged {
     return true;
   }
 
+  template <class T>
   static __device__ void begin(const PcgArgs &a, unsigned char *smem, PipeState &ps) {
     const CsrLayout L = lay(a);
     const int cta = blockIdx.x, tid = threadIdx.x;
@@ -432,29 +483,31 @@ struct OpCsrStaged {
     ps.nc = a.cta_chunk[cta + 1] - ps.c0;
     ps.seq_issue = ps.seq_cons = 0;
     if (tid == 0) {
-      for (int s = 0; s < KQ_STAGES; ++s) mbar_init(reinterpret_cast<uint64_t *>(smem + L.bar) + s, 1);
+      for (int s = 0; s < a.stages; ++s) mbar_init(reinterpret_cast<uint64_t *>(smem + L.bar) + s, 1);
       fence_mbar_init();
     }
     ChunkInfo *tab = reinterpret_cast<ChunkInfo *>(smem + L.tab);
     for (int j = tid; j < min(ps.nc, a.tab_cap); j += blockDim.x) tab[j] = a.chunks[ps.c0 + j];
     const int alo = a.a_lo[cta], na = min(a.a_hi[cta] - alo, a.a_cap);
-    double *arho = reinterpret_cast<double *>(smem + L.arho);
-    double *acs = reinterpret_cast<double *>(smem + L.acs);
-    double *aDl = reinterpret_cast<double *>(smem + L.aDl);
-    double *aDu = reinterpret_cast<double *>(smem + L.aDu);
+    // dose-limit constants of this CTA's rows, in the product arithmetic T
+    T *arho = reinterpret_cast<T *>(smem + L.arho);
+    T *acs = reinterpret_cast<T *>(smem + L.acs);
+    T *aDl = reinterpret_cast<T *>(smem + L.aDl);
+    T *aDu = reinterpret_cast<T *>(smem + L.aDu);
     uint8_t *afl = smem + L.afl;
     for (int i = tid; i < na; i += blockDim.x) {
       const int ai = alo + i;
-      arho[i] = a.P.rhoA[ai];
-      acs[i] = a.cl[ai] + a.cu[ai];
-      aDl[i] = a.Dl[ai];
-      aDu[i] = a.Du[ai];
+      arho[i] = (T)a.P.rhoA[ai];
+      acs[i] = (T)(a.cl[ai] + a.cu[ai]);
+      aDl[i] = (T)a.Dl[ai];
+      aDu[i] = (T)a.Du[ai];
       afl[i] = (uint8_t)((a.P.hasl[ai] ? 1 : 0) | (a.P.hasu[ai] ? 2 : 0));
     }
     __syncthreads();
     if (ps.nc > 0) {
-      for (int s = 0; s < KQ_STAGES - 1; ++s) {
-        if (tid == 0) issue_chunk(a, smem, L, ps);
+      for (int s = 0; s < a.stages - 1; ++s) {
+        if (a.producer == 0) issue_chunk_lsu(a, smem, L, ps);
+        else if (tid == 0) issue_chunk(a, smem, L, ps);
         ps.seq_issue++;
       }
     }
@@ -464,10 +517,187 @@ struct OpCsrStaged {
   // exits with asynchronous writes into its shared memory pending
   static __device__ void drain(const PcgArgs &a, unsigned char *smem, PipeState &ps) {
     const CsrLayout L = lay(a);
+    if (a.producer == 0) {
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      __syncthreads();
+      return;
+    }
     bool ok = true;
-    for (uint32_t s = ps.seq_cons; s < ps.seq_issue; ++s) ok = wait(a, smem, L, s) && ok;
-    if (!ok && threadIdx.x == 0) atomicCAS(a.bar.err, 0, 7);
+    if (threadIdx.x == 0)
+      for (uint32_t s = ps.seq_cons; s < ps.seq_issue; ++s) ok = wait(a, smem, L, s) && ok;
+    if (!ok) atomicCAS(a.bar.err, 0, 7);
     __syncthreads();
+  }
+
+
+  // Row coefficient u_r = w2_r (P_r p) [+ rho (2 t (1/D_l + 1/D_u) + p_l - p_u)
+  // for a dose-limit row; lane 0 writes its bottom entries and adds its share of
+  // p'q to pqt].  All in the product arithmetic T.
+  template <class T>
+  static __device__ __forceinline__ T row_coef(const PcgArgs &a, const RowDesc &d, T dot,
+                                               const double *ysrc, const double *pold,
+                                               double beta, int alo, int na, const T *arho,
+                                               const T *acs, const T *aDl, const T *aDu,
+                                               const T *apl, const T *apu, const uint8_t *afl,
+                                               int lane, T &pqt) {
+    T u;
+    if constexpr (sizeof(T) == 4) u = d.w2hi * dot;
+    else u = ((double)d.w2hi + (double)d.w2lo) * dot;
+    if (d.a >= 0) {
+      const DevProb &P = a.P;
+      const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
+      const int ai = d.a, il = ai - alo;
+      T rho, cs, Dl, Du, pl, pu;
+      int fl;
+      if (il >= 0 && il < na) {
+        rho = arho[il]; cs = acs[il]; Dl = aDl[il]; Du = aDu[il]; fl = afl[il];
+        pl = apl[il]; pu = apu[il];
+      } else {
+        rho = (T)P.rhoA[ai]; cs = (T)(a.cl[ai] + a.cu[ai]); Dl = (T)a.Dl[ai]; Du = (T)a.Du[ai];
+        fl = (P.hasl[ai] ? 1 : 0) | (P.hasu[ai] ? 2 : 0);
+        pl = (T)((fl & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0);
+        pu = (T)((fl & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0);
+      }
+      const T t = rho * dot;
+      const T coef = (T)2 * t * cs + pl - pu;
+      u += rho * coef;
+      if (lane == 0) {
+        const T ql = (fl & 1) ? t + Dl * pl : (T)0;
+        const T qu = (fl & 2) ? -t + Du * pu : (T)0;
+        a.qlam[P.me + ai] = (double)ql;
+        a.qlam[P.me + P.m + ai] = (double)qu;
+        pqt += pl * ql + pu * qu;
+      }
+    }
+    return u;
+  }
+
+  // Rows of one staged chunk: dot with the p window, coefficient, scatter.
+  // Returns this thread's share of p'(K p).  With T = float the per-row
+  // coefficient is formed in FP32 (the FP64 pipe of the SM is narrow) and the
+  // p'q partials are folded into FP64 once per chunk.
+  template <class T, bool WIN>
+  static __device__ double stage_rows(T &pqt, const PcgArgs &a, const double *ysrc, const double *pold,
+                                      double beta, const float *sval, const int *scol,
+                                      const RowDesc *sd, const T *pw, T *acc, T *accg, int lo,
+                                      int alo, int na, const T *arho, const T *acs,
+                                      const T *aDl, const T *aDu, const T *apl,
+                                      const T *apu, const uint8_t *afl, double *s_bcast) {
+    const DevProb &P = a.P;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
+    double pq = 0.0;
+    const int nrows = sd[0].off;
+    if (WIN && sd[0].a < 0 && sd[0].w2hi != 0.f) {
+      // two rows per warp, at most 128 nonzeros each: fixed-trip loops, values
+      // and columns kept in registers between the dot and the scatter
+      for (int i = 2 * warp; i < nrows; i += 2 * nw) {
+        const bool two = i + 1 < nrows;
+        const RowDesc d0 = sd[1 + i];
+        const int e0 = sd[2 + i].off;
+        const RowDesc d1 = two ? sd[2 + i] : d0;
+        const int e1 = two ? sd[3 + i].off : d0.off;
+        float v0[4], v1[4];
+        int c0[4], c1[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int k0 = d0.off + lane + 32 * q, k1 = d1.off + lane + 32 * q;
+          const bool ok0 = k0 < e0, ok1 = k1 < e1;
+          c0[q] = ok0 ? scol[k0] - lo : -1;
+          v0[q] = ok0 ? sval[k0] : 0.f;
+          c1[q] = ok1 ? scol[k1] - lo : -1;
+          v1[q] = ok1 ? sval[k1] : 0.f;
+        }
+        T s0 = (T)0, s1 = (T)0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (c0[q] >= 0) s0 += (T)v0[q] * pw[c0[q]];
+          if (c1[q] >= 0) s1 += (T)v1[q] * pw[c1[q]];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+          s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+        }
+        const T u0 = row_coef<T>(a, d0, s0, ysrc, pold, beta, alo, na, arho, acs, aDl, aDu, apl,
+                                 apu, afl, lane, pqt);
+        const T u1 = two ? row_coef<T>(a, d1, s1, ysrc, pold, beta, alo, na, arho, acs, aDl, aDu,
+                                       apl, apu, afl, lane, pqt)
+                         : (T)0;
+        if (lane == 0) pqt += u0 * s0 + u1 * s1;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (c0[q] >= 0) atomicAdd(acc + c0[q], u0 * (T)v0[q]);
+          if (c1[q] >= 0) atomicAdd(acc + c1[q], u1 * (T)v1[q]);
+        }
+      }
+    } else if (sd[0].a < 0) {
+      for (int i = warp; i < nrows; i += nw) {
+        const RowDesc d = sd[1 + i];
+        const int end = sd[2 + i].off;
+        T dot = (T)0;
+        for (int k = d.off + lane; k < end; k += 32) {
+          const int c = scol[k];
+          T pv;
+          if constexpr (WIN) pv = pw[c - lo];
+          else pv = (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+          dot += (T)sval[k] * pv;
+        }
+        dot = warp_sum(dot);
+        const T u = row_coef<T>(a, d, dot, ysrc, pold, beta, alo, na, arho, acs, aDl, aDu, apl,
+                                apu, afl, lane, pqt);
+        if (lane == 0) pqt += u * dot;
+        for (int k = d.off + lane; k < end; k += 32) {
+          const int c = scol[k];
+          if constexpr (WIN) atomicAdd(acc + (c - lo), u * (T)sval[k]);
+          else atomicAdd(accg + c, u * (T)sval[k]);
+        }
+      }
+    } else {
+      // a single row longer than a stage: whole CTA, straight from global memory
+      const int64_t r = sd[0].a;
+      const RowDesc d = sd[1];
+      const int64_t s = P.rowptr[r], e = P.rowptr[r + 1];
+      double part[1] = {0.0};
+      for (int64_t k = s + tid; k < e; k += blockDim.x) {
+        const int c = P.col[k];
+        T pv;
+        if constexpr (WIN) pv = pw[c - lo];
+        else pv = (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+        part[0] += (double)((T)P.val[k] * pv);
+      }
+      __shared__ double shl[32];
+      block_sum<1>(part, shl);
+      if (tid == 0) {
+        const double dd = part[0];
+        double ud = ((double)d.w2hi + (double)d.w2lo) * dd;
+        if (d.a >= 0) {
+          const int ai = d.a;
+          const double rho = P.rhoA[ai];
+          const int fl = (P.hasl[ai] ? 1 : 0) | (P.hasu[ai] ? 2 : 0);
+          const double pl = (fl & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
+          const double pu = (fl & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
+          const double t = rho * dd;
+          const double coef = 2.0 * t * (a.cl[ai] + a.cu[ai]) + pl - pu;
+          ud += rho * coef;
+          const double ql = (fl & 1) ? t + a.Dl[ai] * pl : 0.0;
+          const double qu = (fl & 2) ? -t + a.Du[ai] * pu : 0.0;
+          a.qlam[P.me + ai] = ql;
+          a.qlam[P.me + P.m + ai] = qu;
+          pq += pl * ql + pu * qu;
+        }
+        pq += ud * dd;
+        s_bcast[0] = ud;
+      }
+      __syncthreads();
+      const T u = (T)s_bcast[0];
+      for (int64_t k = s + tid; k < e; k += blockDim.x) {
+        const int c = P.col[k];
+        if constexpr (WIN) atomicAdd(acc + (c - lo), u * (T)P.val[k]);
+        else atomicAdd(accg + c, u * (T)P.val[k]);
+      }
+    }
+    return pq;
   }
 
   template <class T>
@@ -485,12 +715,12 @@ struct OpCsrStaged {
     T *acc = reinterpret_cast<T *>(smem + L.acc);
     T *accg = reinterpret_cast<T *>(a.accx);
     const int alo = a.a_lo[cta], na = min(a.a_hi[cta] - alo, a.a_cap);
-    const double *arho = reinterpret_cast<const double *>(smem + L.arho);
-    const double *acs = reinterpret_cast<const double *>(smem + L.acs);
-    const double *aDl = reinterpret_cast<const double *>(smem + L.aDl);
-    const double *aDu = reinterpret_cast<const double *>(smem + L.aDu);
-    double *apl = reinterpret_cast<double *>(smem + L.apl);
-    double *apu = reinterpret_cast<double *>(smem + L.apu);
+    const T *arho = reinterpret_cast<const T *>(smem + L.arho);
+    const T *acs = reinterpret_cast<const T *>(smem + L.acs);
+    const T *aDl = reinterpret_cast<const T *>(smem + L.aDl);
+    const T *aDu = reinterpret_cast<const T *>(smem + L.aDu);
+    T *apl = reinterpret_cast<T *>(smem + L.apl);
+    T *apu = reinterpret_cast<T *>(smem + L.apu);
     const uint8_t *afl = smem + L.afl;
     const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
     double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
@@ -503,116 +733,50 @@ struct OpCsrStaged {
     }
     for (int i = tid; i < na; i += blockDim.x) {
       const int ai = alo + i;
-      apl[i] = (afl[i] & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
-      apu[i] = (afl[i] & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
+      apl[i] = (T)((afl[i] & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0);
+      apu[i] = (T)((afl[i] & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0);
     }
     __syncthreads();
     __shared__ double s_bcast[2];
+    T pqt = (T)0;   // FP32 (mixed) share of p'q, folded into FP64 once per product
     for (int j = 0; j < ps.nc; ++j) {
+      if (a.producer == 0) {
+        issue_chunk_lsu(a, smem, L, ps);
+        ps.seq_issue++;
+        cp_async_wait_pending(a.stages - 1);    // the group of seq_cons has landed
+        __syncthreads();
+      } else {
       if (tid == 0) issue_chunk(a, smem, L, ps);
       ps.seq_issue++;
-      const bool w = wait(a, smem, L, ps.seq_cons);
+      // one thread waits (bounded); the others park on the CTA barrier instead
+      // of polling the mbarrier in shared memory, then take the (already
+      // completed) phase with one non-blocking test for acquire ordering
+      bool w = true;
+      if (tid == 0) w = wait(a, smem, L, ps.seq_cons);
       if (__syncthreads_or(!w)) {
         if (tid == 0) atomicCAS(a.bar.err, 0, 7);
         ok = false;
         return 0.0;
       }
-      const int st = (int)(ps.seq_cons % KQ_STAGES);
+      if (tid != 0)
+        (void)mbar_try_wait(reinterpret_cast<uint64_t *>(smem + L.bar) + (ps.seq_cons % (uint32_t)a.stages),
+                            (ps.seq_cons / (uint32_t)a.stages) & 1u);
+      }
+      const int st = (int)(ps.seq_cons % (uint32_t)a.stages);
       const unsigned char *sb = smem + L.stage0 + (size_t)st * L.stage_bytes;
       const float *sval = reinterpret_cast<const float *>(sb + L.val_off);
       const int *scol = reinterpret_cast<const int *>(sb + L.col_off);
       const RowDesc *sd = reinterpret_cast<const RowDesc *>(sb + L.desc_off);
-      const int nrows = sd[0].off;
-      if (sd[0].a == 0) {
-        for (int i = warp; i < nrows; i += nw) {
-          const RowDesc d = sd[1 + i];
-          const int end = sd[2 + i].off;
-          T dot = (T)0;
-          for (int k = d.off + lane; k < end; k += 32) {
-            const int c = scol[k];
-            const T pv = win ? pw[c - lo] : (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
-            dot += (T)sval[k] * pv;
-          }
-          dot = warp_sum(dot);
-          const double dd = (double)dot;
-          double ud = d.w2 * dd;
-          if (d.a >= 0) {
-            const int ai = d.a, il = ai - alo;
-            double rho, cs, Dl, Du, pl, pu;
-            int fl;
-            if (il >= 0 && il < na) {
-              rho = arho[il]; cs = acs[il]; Dl = aDl[il]; Du = aDu[il]; fl = afl[il];
-              pl = apl[il]; pu = apu[il];
-            } else {
-              rho = P.rhoA[ai]; cs = a.cl[ai] + a.cu[ai]; Dl = a.Dl[ai]; Du = a.Du[ai];
-              fl = (P.hasl[ai] ? 1 : 0) | (P.hasu[ai] ? 2 : 0);
-              pl = (fl & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
-              pu = (fl & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
-            }
-            const double t = rho * dd;
-            const double coef = 2.0 * t * cs + pl - pu;
-            ud += rho * coef;
-            if (lane == 0) {
-              const double ql = (fl & 1) ? t + Dl * pl : 0.0;
-              const double qu = (fl & 2) ? -t + Du * pu : 0.0;
-              a.qlam[P.me + ai] = ql;
-              a.qlam[P.me + P.m + ai] = qu;
-              pq += pl * ql + pu * qu;
-            }
-          }
-          if (lane == 0) pq += ud * dd;
-          const T u = (T)ud;
-          for (int k = d.off + lane; k < end; k += 32) {
-            const int c = scol[k];
-            if (win) atomicAdd(acc + (c - lo), u * (T)sval[k]);
-            else atomicAdd(accg + c, u * (T)sval[k]);
-          }
-        }
-      } else {
-        // a single row longer than a stage: whole CTA, straight from global memory
-        const int64_t r = (int64_t)sd[0].w2;
-        const RowDesc d = sd[1];
-        const int64_t s = P.rowptr[r], e = P.rowptr[r + 1];
-        double part[1] = {0.0};
-        for (int64_t k = s + tid; k < e; k += blockDim.x) {
-          const int c = P.col[k];
-          const T pv = win ? pw[c - lo] : (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
-          part[0] += (double)((T)P.val[k] * pv);
-        }
-        __shared__ double shl[32];
-        block_sum<1>(part, shl);
-        if (tid == 0) {
-          const double dd = part[0];
-          double ud = d.w2 * dd;
-          if (d.a >= 0) {
-            const int ai = d.a;
-            const double rho = P.rhoA[ai];
-            const int fl = (P.hasl[ai] ? 1 : 0) | (P.hasu[ai] ? 2 : 0);
-            const double pl = (fl & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
-            const double pu = (fl & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
-            const double t = rho * dd;
-            const double coef = 2.0 * t * (a.cl[ai] + a.cu[ai]) + pl - pu;
-            ud += rho * coef;
-            const double ql = (fl & 1) ? t + a.Dl[ai] * pl : 0.0;
-            const double qu = (fl & 2) ? -t + a.Du[ai] * pu : 0.0;
-            a.qlam[P.me + ai] = ql;
-            a.qlam[P.me + P.m + ai] = qu;
-            pq += pl * ql + pu * qu;
-          }
-          pq += ud * dd;
-          s_bcast[0] = ud;
-        }
-        __syncthreads();
-        const T u = (T)s_bcast[0];
-        for (int64_t k = s + tid; k < e; k += blockDim.x) {
-          const int c = P.col[k];
-          if (win) atomicAdd(acc + (c - lo), u * (T)P.val[k]);
-          else atomicAdd(accg + c, u * (T)P.val[k]);
-        }
-      }
+      if (win)
+        pq += stage_rows<T, true>(pqt, a, ysrc, pold, beta, sval, scol, sd, pw, acc, accg, lo, alo,
+                                  na, arho, acs, aDl, aDu, apl, apu, afl, s_bcast);
+      else
+        pq += stage_rows<T, false>(pqt, a, ysrc, pold, beta, sval, scol, sd, pw, acc, accg, lo, alo,
+                                   na, arho, acs, aDl, aDu, apl, apu, afl, s_bcast);
       __syncthreads();
       ps.seq_cons++;
     }
+    pq += (double)pqt;
     if (win) {
       for (int j = tid; j < wlen; j += blockDim.x) {
         const T v = acc[j];
@@ -660,7 +824,7 @@ __global__ void __launch_bounds__(512, 1) pcg_kernel(PcgArgs a) {
   bool ok = true;
   const double *ysrc = a.apply ? a.rhs : a.y;
   PipeState ps;
-  if constexpr (IsStaged<OP>::value) OP::begin(a, smem, ps);
+  if constexpr (IsStaged<OP>::value) OP::template begin<T>(a, smem, ps);
 
   // ---- initialisation: z = 0, r = rhs, y = r / diag, p_old = 0
   {
@@ -829,6 +993,12 @@ template <class T> KFun pick_kernel(const DevProb &P) {
 
 float g_last_ms = 0.f;
 
+RowDesc split_w2(int32_t off, int32_t a, double w2) {
+  const float hi = (float)w2;
+  const float lo = (float)(w2 - (double)hi);
+  return RowDesc{off, a, hi, lo};
+}
+
 template <class X> X *dalloc(kq_problem *h, size_t count) {
   void *p = nullptr;
   if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(X)) != cudaSuccess) return nullptr;
@@ -856,6 +1026,9 @@ kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double t
   a.chunks = W.chunks; a.cta_chunk = W.cta_chunk; a.rdesc = W.rdesc;
   a.a_lo = W.a_lo; a.a_hi = W.a_hi;
   a.a_cap = W.a_cap; a.ch_cap = W.ch_cap; a.desc_cap = W.desc_cap; a.tab_cap = W.tab_cap;
+  a.copy_piece = W.copy_piece;
+  a.stages = W.stages;
+  a.producer = W.producer;
   KFun f = prec == KQ_PREC_MIXED ? pick_kernel<float>(h->P) : pick_kernel<double>(h->P);
   KQ_CUDA(h, cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)W.smem));
@@ -959,8 +1132,18 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
     int wmax = 0;
     for (int c = 0; c < G; ++c) wmax = std::max(wmax, hi[c] - lo[c]);
     // ---- chunk tables for the staged kernel
-    const int ch_cap = 4096;             // values (and columns) per stage
-    const int desc_cap = 128;            // descriptors per stage
+    // ring geometry (defaults; KQ_CHUNK / KQ_STAGES / KQ_COPY_PIECE override for tuning)
+    auto env_int = [](const char *k, int d) { const char *v = getenv(k); return v ? atoi(v) : d; };
+    const int ch_cap = std::max(256, std::min(16384, env_int("KQ_CHUNK", 4096))) & ~3;
+    W.stages = std::max(2, std::min(KQ_MAX_STAGES, env_int("KQ_STAGES", 4)));
+    W.copy_piece = std::max(16, env_int("KQ_COPY_PIECE", ch_cap * 4)) & ~15;
+    {
+      const char *pr = getenv("KQ_PRODUCER");
+      W.producer = (pr && std::string(pr) == "bulk") ? 1 : 0;
+    }
+    const int desc_cap = std::max(8, ch_cap / 32);  // descriptors per stage
+    // two rows per warp per chunk keeps the warps of a CTA evenly loaded
+    const int rows_per_chunk = std::min(desc_cap - 2, 2 * (threads / 32));
     std::vector<int32_t> p2a(P.nP);
     std::vector<double> w2(P.nP);
     KQ_CUDA(h, cudaMemcpy(p2a.data(), P.prow2a, P.nP * sizeof(int32_t), cudaMemcpyDeviceToHost));
@@ -980,25 +1163,29 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
         const int64_t s_al = s0 & ~(int64_t)3;   // 16-byte aligned start
         if (rp[r + 1] - s_al + 4 > ch_cap) {
           // over-long row: processed from global memory by the whole CTA
-          desc.push_back(RowDesc{1, 1, (double)r});
-          desc.push_back(RowDesc{0, p2a[r], w2[r]});
-          desc.push_back(RowDesc{0, 0, 0.0});
+          desc.push_back(RowDesc{1, (int32_t)r, 0.f, 0.f});
+          desc.push_back(split_w2(0, p2a[r], w2[r]));
+          desc.push_back(RowDesc{0, 0, 0.f, 0.f});
           ci.src = 0;
           ci.nelem = 0;
           if (p2a[r] >= 0) { amin = std::min(amin, p2a[r]); amax = std::max(amax, p2a[r]); }
           ++r;
         } else {
-          desc.push_back(RowDesc{0, 0, (double)r});
+          desc.push_back(RowDesc{0, -1, 0.f, 0.f});
           int nr = 0;
-          while (r < rb[c + 1] && nr < desc_cap - 2 && rp[r + 1] - s_al + 4 <= ch_cap) {
-            desc.push_back(RowDesc{(int32_t)(rp[r] - s_al), p2a[r], w2[r]});
+          while (r < rb[c + 1] && nr < rows_per_chunk && rp[r + 1] - s_al + 4 <= ch_cap) {
+            desc.push_back(split_w2((int32_t)(rp[r] - s_al), p2a[r], w2[r]));
             if (p2a[r] >= 0) { amin = std::min(amin, p2a[r]); amax = std::max(amax, p2a[r]); }
             ++nr;
             ++r;
           }
           const int64_t e = rp[r];
-          desc.push_back(RowDesc{(int32_t)(e - s_al), 0, 0.0});
+          desc.push_back(RowDesc{(int32_t)(e - s_al), 0, 0.f, 0.f});
           desc[ci.desc0].off = nr;
+          // header.w2hi = 1: every row of the chunk has at most 128 nonzeros
+          bool short_rows = true;
+          for (int64_t q = r - nr; q < r; ++q) short_rows = short_rows && (rp[q + 1] - rp[q] <= 128);
+          desc[ci.desc0].w2hi = short_rows ? 1.f : 0.f;
           ci.src = s_al;
           ci.nelem = (int32_t)(((e - s_al) + 3) & ~(int64_t)3);
         }
@@ -1012,16 +1199,32 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
       a_max = std::max(a_max, ahi[c] - alo[c]);
     }
     cta_chunk[G] = (int32_t)chunks.size();
-    W.ch_cap = ch_cap;
-    W.desc_cap = desc_cap;
+    // stages sized to the largest chunk actually built, not the cap
+    int used_elems = 4, used_desc = 3;
+    for (const ChunkInfo &ci : chunks) {
+      used_elems = std::max(used_elems, (int)ci.nelem);
+      used_desc = std::max(used_desc, (int)ci.ndesc);
+    }
+    W.ch_cap = (used_elems + 31) & ~31;
+    W.desc_cap = (used_desc + 7) & ~7;
     W.tab_cap = std::min(max_nc, 512);
     W.a_cap = std::min(a_max, 1024);
-    // shared memory: window + A rows + chunk table + stages; shrink the window if needed
+    // shared memory: column window + A rows + chunk table + ring.  Keep the
+    // whole window if possible and give the rest to ring stages (up to 8, or
+    // KQ_STAGES if set); shrink the window only if two stages do not fit.
     const size_t limit = 220 * 1024;
     win_cap = wmax;
-    while (csr_layout(win_cap, W.a_cap, ch_cap, desc_cap, W.tab_cap).total > limit && win_cap > 0)
+    if (!getenv("KQ_STAGES")) {
+      W.stages = 2;
+      while (W.stages < KQ_MAX_STAGES &&
+             csr_layout(win_cap, W.a_cap, W.ch_cap, W.desc_cap, W.tab_cap, W.stages + 1).total <= limit)
+        ++W.stages;
+    }
+    while (csr_layout(win_cap, W.a_cap, W.ch_cap, W.desc_cap, W.tab_cap, W.stages).total > limit &&
+           win_cap > 0)
       win_cap = win_cap > 1024 ? win_cap - 1024 : 0;
-    smem = csr_layout(win_cap, W.a_cap, ch_cap, desc_cap, W.tab_cap).total;
+    smem = csr_layout(win_cap, W.a_cap, W.ch_cap, W.desc_cap, W.tab_cap, W.stages).total;
+    if (smem > limit) return kq_fail(h, KQ_ERR_ARG, "CSR staging ring does not fit in shared memory");
     W.chunks = dalloc<ChunkInfo>(h, chunks.size());
     W.rdesc = dalloc<RowDesc>(h, desc.size());
     W.cta_chunk = dalloc<int32_t>(h, G + 1);

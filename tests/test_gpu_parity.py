@@ -148,6 +148,10 @@ def test_ipm_matches_oracle(kq, name, prec):
     met = oracle.kkt_metrics(qp, out["x"], out["lam_lA"], out["lam_uA"], out["lam_lx"],
                              out["lam_ux"], out["lam_e"])
     assert met["kkt_rel"] <= 1e-6, met
+    # same mu path: complementarity of the same size as the oracle's
+    from oracle.metrics import full_multipliers
+    ref = oracle.kkt_metrics(qp, res.x, *full_multipliers(res.scaled, res.lam, qp))
+    assert met["compl_rel"] <= 2.0 * ref["compl_rel"] + 1e-12, (met, ref)
     assert st.mu_final == pytest.approx(res.mu)
 
 
