@@ -370,7 +370,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,
-                         "kernel": "pcg_kernel<OpCsr> (persistent PCG solve)",
+                         "kernel": "pcg_kernel<OpCsrStaged> (persistent PCG solve)",
                          "algorithmic_bytes_per_product": abytes, "note": ALGO_BYTES_NOTE},
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
