@@ -218,6 +218,31 @@ kq_status qp_sizes(kq_handle h, int64_t *n, int64_t *m, int64_t *me, int64_t *nk
 const char *qp_last_error(kq_handle h);
 void qp_destroy(kq_handle h);
 
+/* kkt_pcg_solve_static: the same persistent Jacobi-PCG solve of the doubly
+ * augmented system, for callers that cannot allocate device memory (a fixed,
+ * pre-reserved memory budget; an allocator that must not be bypassed).  The
+ * paper has no counterpart; this is a packaging of the library's dense PCG
+ * kernel.  It allocates nothing: its work space is one static device array of
+ * about 0.78 MB that every GPU loading the library holds until the process
+ * exits, shared by all calls.
+ *  n, m      0 < n <= 4096, 0 <= m <= 4096; larger sizes return KQ_ERR_ARG
+ *  H         n x n symmetric (row-major, FP64, device), already scaled
+ *  A         m x n general rows (row-major, FP64, device), all two-sided
+ *  Dl, Du    m each (device): the D blocks, finite and > 0 (else KQ_ERR_ARG)
+ *  dg        n (device): the bound term of Q = H + diag(dg)
+ *  rhs, sol  n + 2m (device), layout [x | lam_l | lam_u]; z0 = 0
+ *  tol       relative unpreconditioned residual; maxit iterations
+ *  stream    cudaStream_t or NULL; *iters, *rel_res (recursive) may be NULL
+ * The first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  The array keeps the last call's
+ * contents (its counters are cleared on entry), so calls that overlap on the
+ * GPU race: serialise them.  KQ_WARN_PCG_MAXIT if the tolerance was not met;
+ * errors are reported by kq_global_error(). */
+kq_status kkt_pcg_solve_static(int64_t n, int64_t m, const double *H, const double *A,
+                               const double *Dl, const double *Du, const double *dg,
+                               const double *rhs, double *sol, double tol, int maxit,
+                               void *stream, int *iters, double *rel_res);
+
 /* Library-wide: message of the last failure of a call that had no handle
  * (qp_create). */
 const char *kq_global_error(void);

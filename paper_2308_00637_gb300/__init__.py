@@ -111,6 +111,8 @@ def load(path: str = LIB_PATH):
         "qp_last_error": (C.c_char_p, [P]),
         "qp_destroy": (None, [P]),
         "kq_global_error": (C.c_char_p, []),
+        "kkt_pcg_solve_static": (I, [I64, I64, P, P, P, P, P, P, P, D, I, P, C.POINTER(C.c_int),
+                                     C.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -247,6 +249,20 @@ def qp_residuals(h: Handle, **bufs):
     norm = C.c_double()
     h.check(load().qp_residuals(h.h, *[_ptr(bufs.get(k)) for k in keys], C.byref(norm)))
     return norm.value
+
+
+def kkt_pcg_solve_static(n, m, H, A, Dl, Du, dg, rhs, sol, tol=1e-7, maxit=5000, stream=None,
+                         allow=(KQ_OK, KQ_WARN_PCG_MAXIT)):
+    """Allocation-free dense PCG solve (all buffers are device tensors)."""
+    it = C.c_int()
+    rel = C.c_double()
+    lib = load()
+    rc = lib.kkt_pcg_solve_static(int(n), int(m), _ptr(H), _ptr(A), _ptr(Dl), _ptr(Du), _ptr(dg),
+                                  _ptr(rhs), _ptr(sol), float(tol), int(maxit), stream,
+                                  C.byref(it), C.byref(rel))
+    if rc not in allow:
+        raise KQError(rc, lib.kq_global_error().decode())
+    return rc, it.value, rel.value
 
 
 def qp_scaling(h: Handle):

@@ -179,6 +179,18 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
 // out = K v in FP64 (prec = KQ_PREC_F64) or mixed arithmetic.
 kq_status pcg_apply(kq_problem *h, const double *v, double *out, int prec, float *ms);
 double pcg_last_kernel_ms();
+// Work buffers of one persistent PCG launch, provided by the caller.
+struct PcgRawWork {
+  double *r, *y, *pb0, *pb1, *qlam, *slots, *resn;
+  void *accx;
+  unsigned int *bar;
+  int *err, *iters;
+};
+kq_status pcg_dense_raw(const DevProb &P, const double *Dl, const double *Du, const double *cl,
+                        const double *cu, const double *dg, const double *diag, const double *rhs,
+                        double *z, const PcgRawWork &w, int G, double tol, int maxit,
+                        double timeout_s, cudaStream_t stream, int *iters, double *rr,
+                        double *bb, std::string *msg);
 
 // ipm kernels (ipm.cu)
 kq_status kkt_assemble(kq_problem *h);   // residuals, rhs, D, diag at state & mu

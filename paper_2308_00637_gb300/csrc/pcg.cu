@@ -1073,6 +1073,56 @@ double dev_norm(kq_problem *h, const double *v, int64_t N) {
 
 }  // namespace
 
+// Persistent PCG on a dense problem whose blocks and work buffers the caller
+// supplies (device pointers); launches, copies two status words back, and
+// allocates nothing.
+kq_status pcg_dense_raw(const DevProb &P, const double *Dl, const double *Du, const double *cl,
+                        const double *cu, const double *dg, const double *diag, const double *rhs,
+                        double *z, const PcgRawWork &w, int G, double tol, int maxit,
+                        double timeout_s, cudaStream_t stream, int *iters, double *rr,
+                        double *bb, std::string *msg) {
+  PcgArgs a{};
+  a.P = P;
+  a.Dl = Dl; a.Du = Du; a.cl = cl; a.cu = cu; a.dg = dg; a.diag = diag; a.mu = 1.0;
+  a.rhs = rhs; a.z = z;
+  a.r = w.r; a.y = w.y; a.pb0 = w.pb0; a.pb1 = w.pb1; a.qlam = w.qlam;
+  a.accx = w.accx; a.g = nullptr; a.slots = w.slots;
+  a.row_begin = nullptr; a.win_lo = nullptr; a.win_hi = nullptr; a.win_cap = (int)P.n;
+  a.bar.count = w.bar; a.bar.gen = w.bar + 1; a.bar.err = w.err; a.bar.nblocks = (unsigned)G;
+  a.bar.budget_ns = (uint64_t)(timeout_s * 1e9);
+  a.tol2 = tol * tol; a.maxit = maxit; a.apply = 0;
+  a.iters = w.iters; a.resn = w.resn;
+  a.stages = 2; a.producer = 0; a.copy_piece = 16;
+  KFun f = pcg_kernel<OpDense<double, double>, double>;
+  const size_t smem = (size_t)2 * P.n * sizeof(double);
+  const int threads = 512;
+  auto fail = [&](const char *what, cudaError_t e) {
+    if (msg) *msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return KQ_ERR_CUDA;
+  };
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+    return fail("cudaFuncSetAttribute", e);
+  void *args[] = {&a};
+  if ((e = cudaLaunchCooperativeKernel((const void *)f, dim3(G), dim3(threads), args, smem, stream)) != cudaSuccess)
+    return fail("cudaLaunchCooperativeKernel", e);
+  int hs[2] = {0, 0};
+  double hr[2] = {0.0, 0.0};
+  if ((e = cudaMemcpyAsync(&hs[0], w.err, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&hs[1], w.iters, sizeof(int), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(hr, w.resn, 2 * sizeof(double), cudaMemcpyDeviceToHost, stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(stream)) != cudaSuccess)
+    return fail("status read-back", e);
+  if (iters) *iters = hs[1];
+  if (rr) *rr = hr[0];
+  if (bb) *bb = hr[1];
+  if (hs[0] == 7) { if (msg) *msg = "grid barrier exceeded its time budget"; return KQ_ERR_TIMEOUT; }
+  if (hs[0] == 4) { if (msg) *msg = "p'Kp <= 0 (K not positive definite)"; return KQ_ERR_NOT_CONVEX; }
+  if (hs[0] == 8) { if (msg) *msg = "NaN in PCG"; return KQ_ERR_NUMERIC; }
+  if (hs[0] != 0) { if (msg) *msg = "PCG error flag"; return KQ_ERR_CUDA; }
+  return KQ_OK;
+}
+
 double pcg_last_kernel_ms() { return g_last_ms; }
 
 kq_status pcg_setup(kq_problem *h, int grid_ctas) {
