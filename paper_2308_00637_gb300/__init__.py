@@ -340,6 +340,64 @@ def create_from(qp, device_tensors: bool = False, stream=None) -> Handle:
     return h
 
 
+def _qp_torch_layer():
+    """Build the torch.autograd.Function lazily (torch is optional for the
+    plain C-ABI binding)."""
+    import torch
+
+    class QPFunction(torch.autograd.Function):
+        """x* = argmin of the QP with linear term p, row bounds lA/uA and
+        equality right-hand side b (the structure H, A, C and the variable
+        bounds come from ``qp``).  Forward: qp_create + ipm_solve on the GPU.
+        Backward: qp_backward, one PCG solve with the converged KKT matrix
+        (Eq. (9)); gradients in original units, zero for absent bounds."""
+
+        @staticmethod
+        def forward(ctx, p, lA, uA, b, qp, opts):
+            import copy
+            q2 = copy.copy(qp)
+            q2.p = p.detach().double().cpu().numpy()
+            if qp.akind != "none":
+                q2.lA = lA.detach().double().cpu().numpy()
+                q2.uA = uA.detach().double().cpu().numpy()
+            if qp.C is not None and qp.C.shape[0]:
+                q2.b = b.detach().double().cpu().numpy()
+            h = create_from(q2)
+            x = torch.zeros(h.n, dtype=torch.float64, device=p.device)
+            ipm_solve(h, opts, x=x)
+            ctx.h = h
+            ctx.devices = p.device
+            return x
+
+        @staticmethod
+        def backward(ctx, gx):
+            h = ctx.h
+            dev = ctx.devices
+            g = gx.detach().double().contiguous()
+            gp = torch.zeros(h.n, dtype=torch.float64, device=dev)
+            glA = torch.zeros(h.m, dtype=torch.float64, device=dev)
+            guA = torch.zeros(h.m, dtype=torch.float64, device=dev)
+            gb = torch.zeros(h.me, dtype=torch.float64, device=dev)
+            qp_backward(h, g.to(dev), gp, glA if h.m else None, guA if h.m else None,
+                        gb if h.me else None)
+            torch.cuda.synchronize()
+            qp_destroy(h)
+            return gp, glA, guA, gb, None, None
+
+    return QPFunction
+
+
+_QPF = None
+
+
+def qp_layer(qp, p, lA, uA, b, opts: Optional[KqIpmOpts] = None):
+    """Differentiable QP solution x*(p, lA, uA, b) (torch tensors on cuda)."""
+    global _QPF
+    if _QPF is None:
+        _QPF = _qp_torch_layer()
+    return _QPF.apply(p, lA, uA, b, qp, opts)
+
+
 def solve(qp, opts: Optional[KqIpmOpts] = None, allow=(KQ_OK,)):
     """Create, solve and return (status, stats, x, multipliers dict)."""
     h = create_from(qp)
