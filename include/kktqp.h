@@ -218,6 +218,52 @@ kq_status qp_sizes(kq_handle h, int64_t *n, int64_t *m, int64_t *me, int64_t *nk
 const char *qp_last_error(kq_handle h);
 void qp_destroy(kq_handle h);
 
+/* ------------------------------------------------------------------------
+ * Batched solve of many dense QPs of uneven size (Algorithm 1 in lock step
+ * over the batch; each IPM iteration runs ONE persistent PCG launch for every
+ * QP still iterating, with teams of CTAs sized by each QP's bytes per K*v
+ * product).  The paper solves one QP at a time; batching is this library's
+ * packaging of the same method.
+ * ------------------------------------------------------------------------ */
+typedef struct kq_batch_s *kq_batch;
+
+/* One QP of a batch: the arguments of qp_create (H must be DENSE; every QP of a
+ * batch stores H and A in the same types: BF16 H with F32 A, or F64 / F64). */
+typedef struct {
+  int64_t n;
+  kq_hop H;
+  const double *p;
+  kq_amat A;             /* kind KQ_A_NONE for no general rows                */
+  const double *lA, *uA;
+  int64_t me;
+  const double *C, *b;
+  const double *lx, *ux;
+} kq_qp_desc;
+
+typedef struct {
+  int converged;         /* QPs that met the mu rule                          */
+  int ipm_iters_max;     /* lock-step IPM iterations run                      */
+  long long ipm_iters_total;
+  long long pcg_iters;   /* summed over QPs                                   */
+  int pcg_maxit_hits;
+  int max_active;
+  double pcg_kernel_ms;  /* device time of the batched PCG launches           */
+  long long pcg_launches;
+  double time_s;
+} kq_batch_stats;
+
+/* Create nqp QPs (copies of the inputs, as qp_create) ordered on `stream`. */
+kq_status qp_create_batch(kq_batch *out, int nqp, const kq_qp_desc *descs, void *stream);
+/* Solve all QPs from their initial points.  x: nqp pointers (host or device,
+ * n_i doubles each, original units; NULL entries skipped).  status: nqp codes
+ * (KQ_OK or KQ_ERR_IPM_MAXIT).  Returns KQ_OK when every QP converged. */
+kq_status ipm_solve_batch(kq_batch b, const kq_ipm_opts *opts, double *const *x, int *status,
+                          kq_batch_stats *stats);
+kq_status qp_batch_info(kq_batch b, int *nqp, int64_t *n);
+const char *qp_batch_last_error(kq_batch b);
+const char *kq_batch_error(void);
+void qp_batch_destroy(kq_batch b);
+
 /* kkt_pcg_solve_static: the same persistent Jacobi-PCG solve of the doubly
  * augmented system, for callers that cannot allocate device memory (a fixed,
  * pre-reserved memory budget; an allocator that must not be bypassed).  The

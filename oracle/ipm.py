@@ -129,7 +129,7 @@ def scale(qp) -> Scaled:
     """Objective scaling by sigma and 2-norm row scaling of A and C."""
     n = qp.n
     if qp.hkind == "dense":
-        H = np.asarray(qp.H, dtype=np.float64)
+        H = qp.H_dense()
         hmax = float(np.max(np.diag(H))) if n else 0.0
     elif qp.hkind == "csr_lsq":
         P = qp.P.astype(np.float64)

@@ -35,7 +35,7 @@ def objective(qp, x):
 
 def _Hx(qp, x):
     if qp.hkind == "dense":
-        return np.asarray(qp.H, float) @ x
+        return qp.H_dense() @ x
     if qp.hkind == "csr_lsq":
         P = qp.P.astype(np.float64)
         return 2.0 * (P.T @ (qp.w * (P @ x)))

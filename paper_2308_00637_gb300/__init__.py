@@ -407,3 +407,117 @@ def solve(qp, opts: Optional[KqIpmOpts] = None, allow=(KQ_OK,)):
     rc, st = ipm_solve(h, opts, **out, allow=allow)
     qp_destroy(h)
     return rc, st, out
+
+
+# ---------------------------------------------------------------- batched QPs
+class KqQpDesc(C.Structure):
+    _fields_ = [("n", C.c_int64), ("H", KqHop), ("p", C.c_void_p), ("A", KqAmat),
+                ("lA", C.c_void_p), ("uA", C.c_void_p), ("me", C.c_int64), ("C", C.c_void_p),
+                ("b", C.c_void_p), ("lx", C.c_void_p), ("ux", C.c_void_p)]
+
+
+class KqBatchStats(C.Structure):
+    _fields_ = [("converged", C.c_int), ("ipm_iters_max", C.c_int),
+                ("ipm_iters_total", C.c_longlong), ("pcg_iters", C.c_longlong),
+                ("pcg_maxit_hits", C.c_int), ("max_active", C.c_int),
+                ("pcg_kernel_ms", C.c_double), ("pcg_launches", C.c_longlong),
+                ("time_s", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Batch:
+    def __init__(self, b, ns):
+        self.b, self.ns = b, ns
+
+    def __del__(self):
+        try:
+            qp_batch_destroy(self)
+        except Exception:
+            pass
+
+
+def _batch_lib():
+    lib = load()
+    if not hasattr(lib, "_batch_sigs"):
+        P = C.c_void_p
+        lib.qp_create_batch.restype = C.c_int
+        lib.qp_create_batch.argtypes = [C.POINTER(P), C.c_int, C.POINTER(KqQpDesc), P]
+        lib.ipm_solve_batch.restype = C.c_int
+        lib.ipm_solve_batch.argtypes = [P, C.POINTER(KqIpmOpts), C.POINTER(P), C.POINTER(C.c_int),
+                                        C.POINTER(KqBatchStats)]
+        lib.qp_batch_destroy.restype = None
+        lib.qp_batch_destroy.argtypes = [P]
+        lib.qp_batch_last_error.restype = C.c_char_p
+        lib.qp_batch_last_error.argtypes = [P]
+        lib.kq_batch_error.restype = C.c_char_p
+        lib.kq_batch_error.argtypes = []
+        lib._batch_sigs = True
+    return lib
+
+
+def qp_create_batch(qps, stream=None) -> Batch:
+    """Create a batch from problem objects with a dense H (generator layout:
+    H as bf16 bits in meta['H_bf16_bits'] or float64, A dense)."""
+    lib = _batch_lib()
+    keep = []
+
+    def arr(a, dt):
+        x = np.ascontiguousarray(np.asarray(a, dtype=dt))
+        keep.append(x)
+        return x.ctypes.data
+
+    descs = (KqQpDesc * len(qps))()
+    for i, qp in enumerate(qps):
+        d = descs[i]
+        d.n = qp.n
+        bits = qp.meta.get("H_bf16_bits") if qp.meta else None
+        d.H.kind, d.H.rows, d.H.cols = KQ_H_DENSE, qp.n, qp.n
+        if bits is not None:
+            d.H.dtype, d.H.val = KQ_BF16, arr(bits, np.uint16)
+        else:
+            d.H.dtype, d.H.val = KQ_F64, arr(qp.H, np.float64)
+        d.p = arr(qp.p, np.float64)
+        if qp.akind == "dense":
+            Am = np.asarray(qp.A)
+            d.A.kind, d.A.m = KQ_A_DENSE, Am.shape[0]
+            if Am.dtype == np.float32 or (qp.meta or {}).get("a_f32", False):
+                d.A.dtype, d.A.val = KQ_F32, arr(Am, np.float32)
+            else:
+                d.A.dtype, d.A.val = KQ_F64, arr(Am, np.float64)
+            d.lA, d.uA = arr(qp.lA, np.float64), arr(qp.uA, np.float64)
+        else:
+            d.A.kind = KQ_A_NONE
+        d.me = 0 if qp.C is None else qp.C.shape[0]
+        if d.me:
+            d.C, d.b = arr(qp.C, np.float64), arr(qp.b, np.float64)
+        d.lx, d.ux = arr(qp.lx, np.float64), arr(qp.ux, np.float64)
+    b = C.c_void_p()
+    rc = lib.qp_create_batch(C.byref(b), len(qps), descs, stream)
+    if rc != KQ_OK:
+        raise KQError(rc, lib.kq_batch_error().decode())
+    return Batch(b, [qp.n for qp in qps])
+
+
+def ipm_solve_batch(batch: Batch, opts: Optional[KqIpmOpts] = None, xs=None,
+                    allow=(KQ_OK, KQ_ERR_IPM_MAXIT)):
+    lib = _batch_lib()
+    nq = len(batch.ns)
+    ptrs = (C.c_void_p * nq)()
+    if xs is not None:
+        for i, x in enumerate(xs):
+            ptrs[i] = _ptr(x)
+    status = (C.c_int * nq)()
+    st = KqBatchStats()
+    rc = lib.ipm_solve_batch(batch.b, C.byref(opts) if opts is not None else None, ptrs, status,
+                             C.byref(st))
+    if rc not in allow:
+        raise KQError(rc, lib.qp_batch_last_error(batch.b).decode())
+    return rc, list(status), st
+
+
+def qp_batch_destroy(batch: Batch):
+    if batch is not None and batch.b:
+        _batch_lib().qp_batch_destroy(batch.b)
+        batch.b = None

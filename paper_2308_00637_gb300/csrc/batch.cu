@@ -1,0 +1,290 @@
+// Batched solve of many dense convex QPs of uneven size (Algorithm 1 run in
+// lock step over the batch).  Each QP keeps its own device data (created with
+// qp_create on the batch's stream); per IPM iteration the whole batch shares
+// ONE persistent PCG launch in which teams of CTAs, sized by each QP's bytes
+// per product, run the QPs' Jacobi-PCG solves concurrently (pcg.cu).  The
+// per-QP residual, recovery and update kernels are enqueued for every active
+// QP with one host synchronisation per phase.
+#include "common.cuh"
+#include "kq_internal.h"
+#include <chrono>
+#include <cstdio>
+#include <cmath>
+#include <string>
+#include <vector>
+
+struct kq_batch_s {
+  cudaStream_t stream = nullptr;
+  std::vector<kq_problem *> qps;
+  BatchPcg B;
+  std::string err;
+  int max_n = 0;
+};
+
+namespace {
+thread_local std::string g_batch_err;
+
+kq_status bfail(kq_batch b, kq_status st, const std::string &msg) {
+  if (b) b->err = msg;
+  else g_batch_err = msg;
+  return st;
+}
+
+// Batched Jacobi-PCG with the same refinement as the single-problem solver:
+// z = 0; res = rhs; passes of {solve K dz = res (FP32 products while the
+// refinement budget lasts, then FP64); z += dz; res = rhs - K z in FP64}.
+kq_status batch_pcg(kq_batch b, const std::vector<int> &act, const kq_pcg_opts &o,
+                    std::vector<long long> &iters_out, std::vector<int> &maxit_hit,
+                    double *kernel_ms, const std::vector<double> &last_iters) {
+  auto &hs = b->qps;
+  const int k = (int)act.size();
+  cudaStream_t s = b->stream;
+  std::vector<double> bnorm(k, 0.0), resn(k, 0.0);
+  std::vector<int> used(k, 0), done(k, 0);
+  iters_out.assign(k, 0);
+  maxit_hit.assign(k, 0);
+  for (int j = 0; j < k; ++j) {
+    kq_problem *h = hs[act[j]];
+    if (cudaMemsetAsync(h->z, 0, h->nkp * sizeof(double), s) != cudaSuccess ||
+        cudaMemcpyAsync(h->tmp, h->K.rhs, h->nkp * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return bfail(b, KQ_ERR_CUDA, "batch PCG init");
+  }
+  const int mixed = o.precision == KQ_PREC_MIXED;
+  const int max_passes = (mixed ? o.refine_steps : 0) + 3;
+  for (int pass = 0; pass < max_passes; ++pass) {
+    const int prec = (mixed && pass < o.refine_steps) ? KQ_PREC_MIXED : KQ_PREC_F64;
+    std::vector<int> idx;
+    std::vector<const double *> rhs;
+    std::vector<double *> out;
+    std::vector<double> tol;
+    std::vector<int> maxit;
+    std::vector<int> map;
+    std::vector<double> wts;
+    for (int j = 0; j < k; ++j) {
+      if (done[j]) continue;
+      const int budget = o.maxit - used[j];
+      if (budget <= 0) { done[j] = 1; continue; }
+      kq_problem *h = hs[act[j]];
+      double rel = pass == 0 ? o.tol : o.tol * bnorm[j] / std::max(resn[j], 1e-300);
+      if (prec == KQ_PREC_MIXED) rel = std::max(rel, o.inner_tol);
+      rel = std::min(rel, 0.5);
+      idx.push_back(act[j]);
+      rhs.push_back(h->tmp);
+      out.push_back(h->zref);
+      tol.push_back(rel);
+      maxit.push_back(budget);
+      map.push_back(j);
+      wts.push_back(last_iters[act[j]]);
+    }
+    if (idx.empty()) break;
+    std::vector<int> its, errs;
+    std::vector<double> rr, bb;
+    float ms = 0.f;
+    std::string e;
+    kq_status rc = batch_pcg_launch(b->B, hs, idx, rhs, out, tol, maxit, 0, prec, s, its, errs, rr,
+                                    bb, &ms, e, &wts);
+    if (rc != KQ_OK) return bfail(b, rc, e);
+    *kernel_ms += ms;
+    for (size_t q = 0; q < idx.size(); ++q) {
+      const int j = map[q];
+      if (errs[q] != 0)
+        return bfail(b, errs[q] == 7 ? KQ_ERR_TIMEOUT : (errs[q] == 4 ? KQ_ERR_NOT_CONVEX : KQ_ERR_NUMERIC),
+                     "batched PCG failed on QP " + std::to_string(act[j]));
+      if (pass == 0) bnorm[j] = std::sqrt(bb[q]);
+      used[j] += its[q];
+      iters_out[j] += its[q];
+      kq_problem *h = hs[act[j]];
+      vec_add_enqueue(h, h->z, h->zref);
+    }
+    // FP64 K z for every QP of this pass in one launch, then res = rhs - K z
+    std::vector<const double *> zin;
+    std::vector<double *> kz;
+    for (size_t q = 0; q < idx.size(); ++q) {
+      kq_problem *h = hs[idx[q]];
+      zin.push_back(h->z);
+      kz.push_back(h->zref);
+    }
+    std::vector<double> tol0(idx.size(), 0.0);
+    std::vector<int> mx0(idx.size(), 0);
+    rc = batch_pcg_launch(b->B, hs, idx, zin, kz, tol0, mx0, 1, KQ_PREC_F64, s, its, errs, rr, bb,
+                          &ms, e);
+    if (rc != KQ_OK) return bfail(b, rc, e);
+    *kernel_ms += ms;
+    for (size_t q = 0; q < idx.size(); ++q) {
+      kq_problem *h = hs[idx[q]];
+      vec_resid_enqueue(h, h->K.rhs, h->zref, h->tmp);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return bfail(b, KQ_ERR_CUDA, "batch PCG sync");
+    for (size_t q = 0; q < idx.size(); ++q) {
+      const int j = map[q];
+      resn[j] = std::sqrt(hs[idx[q]]->h_red[8]);
+      if (!(resn[j] == resn[j])) return bfail(b, KQ_ERR_NUMERIC, "batched PCG residual NaN");
+      if (resn[j] <= o.tol * bnorm[j] || bnorm[j] == 0.0) done[j] = 1;
+      else if (used[j] >= o.maxit) { done[j] = 1; maxit_hit[j] = 1; }
+    }
+  }
+  for (int j = 0; j < k; ++j)
+    if (resn[j] > o.tol * bnorm[j]) maxit_hit[j] = 1;
+  return KQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *kq_batch_error(void) { return g_batch_err.c_str(); }
+const char *qp_batch_last_error(kq_batch b) { return b ? b->err.c_str() : g_batch_err.c_str(); }
+
+void qp_batch_destroy(kq_batch b) {
+  if (!b) return;
+  for (kq_problem *h : b->qps) qp_destroy(h);
+  batch_pcg_free(b->B);
+  delete b;
+}
+
+kq_status qp_create_batch(kq_batch *out, int nqp, const kq_qp_desc *d, void *stream) {
+  if (!out || nqp <= 0 || !d) return bfail(nullptr, KQ_ERR_ARG, "qp_create_batch: bad arguments");
+  *out = nullptr;
+  kq_batch b = new kq_batch_s();
+  b->stream = (cudaStream_t)stream;
+  for (int i = 0; i < nqp; ++i) {
+    if (d[i].H.kind != KQ_H_DENSE) {
+      qp_batch_destroy(b);
+      return bfail(nullptr, KQ_ERR_ARG, "qp_create_batch: every QP needs a dense H");
+    }
+    kq_handle h = nullptr;
+    const kq_status st = qp_create(&h, d[i].n, &d[i].H, d[i].p, d[i].A.kind == KQ_A_NONE ? nullptr : &d[i].A,
+                                   d[i].lA, d[i].uA, d[i].me, d[i].C, d[i].b, d[i].lx, d[i].ux, stream);
+    if (st != KQ_OK) {
+      const std::string msg = "qp_create_batch: QP " + std::to_string(i) + ": " + kq_global_error();
+      qp_batch_destroy(b);
+      return bfail(nullptr, st, msg);
+    }
+    b->qps.push_back(h);
+    b->max_n = std::max<int>(b->max_n, (int)d[i].n);
+  }
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  std::string e;
+  const kq_status st = batch_pcg_setup(b->B, nqp, sms, b->max_n, e);
+  if (st != KQ_OK) {
+    qp_batch_destroy(b);
+    return bfail(nullptr, st, "qp_create_batch: " + e);
+  }
+  *out = b;
+  return KQ_OK;
+}
+
+kq_status qp_batch_info(kq_batch b, int *nqp, int64_t *n) {
+  if (!b) return bfail(nullptr, KQ_ERR_ARG, "null batch");
+  if (nqp) *nqp = (int)b->qps.size();
+  if (n)
+    for (size_t i = 0; i < b->qps.size(); ++i) n[i] = b->qps[i]->n;
+  return KQ_OK;
+}
+
+kq_status ipm_solve_batch(kq_batch b, const kq_ipm_opts *opts, double *const *x, int *status,
+                          kq_batch_stats *stats) {
+  if (!b) return bfail(nullptr, KQ_ERR_ARG, "null batch");
+  auto t0 = std::chrono::steady_clock::now();
+  kq_ipm_opts o;
+  kq_default_ipm_opts(&o);
+  if (opts) o = *opts;
+  kq_pcg_opts po;
+  po.tol = o.pcg_tol; po.maxit = o.pcg_maxit; po.precision = o.precision;
+  po.refine_steps = o.refine_steps; po.inner_tol = o.inner_tol;
+  auto &hs = b->qps;
+  const int nq = (int)hs.size();
+  cudaStream_t s = b->stream;
+  kq_batch_stats st{};
+  std::vector<double> mu(nq, o.mu0);
+  std::vector<int> kexp(nq, 0), done(nq, 0), stat(nq, KQ_ERR_IPM_MAXIT), iters(nq, 0);
+  for (kq_problem *h : hs) {
+    h->timeout_s = o.timeout_s > 0 ? o.timeout_s : 2.0;
+    h->solved = false;
+    h->state_set = false;
+    h->mu = o.mu0;
+    if (init_state(h) != KQ_OK || assemble_enqueue(h) != KQ_OK) return bfail(b, KQ_ERR_CUDA, h->err);
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return bfail(b, KQ_ERR_CUDA, "batch init");
+  double n2;
+  for (kq_problem *h : hs) assemble_finish(h, &n2, nullptr);
+  double kernel_ms = 0.0;
+  std::vector<double> last_iters(nq, 1.0);   // PCG iterations of each QP's previous solve
+  int it;
+  for (it = 1; it <= o.ipm_maxit; ++it) {
+    std::vector<int> act;
+    for (int i = 0; i < nq; ++i) if (!done[i]) act.push_back(i);
+    if (act.empty()) break;
+    st.max_active = std::max(st.max_active, (int)act.size());
+    std::vector<long long> pits;
+    std::vector<int> hit;
+    const double kms0 = kernel_ms;
+    const kq_status rc = batch_pcg(b, act, po, pits, hit, &kernel_ms, last_iters);
+    if (rc != KQ_OK) return rc;
+    long long its_sum = 0;
+    for (size_t j = 0; j < act.size(); ++j) {
+      st.pcg_iters += pits[j];
+      st.pcg_maxit_hits += hit[j];
+      last_iters[act[j]] = (double)std::max<long long>(1, pits[j]);
+      its_sum += pits[j];
+    }
+    if (o.verbose) {
+      fprintf(stderr, "batch ipm %3d active %4zu pcg iters %8lld pcg %.1f ms\n", it, act.size(),
+              its_sum, kernel_ms - kms0);
+      fflush(stderr);
+    }
+    for (int i : act)
+      if (recover_enqueue(hs[i]) != KQ_OK) return bfail(b, KQ_ERR_CUDA, hs[i]->err);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return bfail(b, KQ_ERR_CUDA, "batch recover");
+    for (int i : act) {
+      double ax, al;
+      recover_finish(hs[i], o.gamma, &ax, &al);
+      if (!(ax == ax) || !(al == al)) return bfail(b, KQ_ERR_NUMERIC, "NaN step length");
+      if (update_enqueue(hs[i], ax, al) != KQ_OK || assemble_enqueue(hs[i]) != KQ_OK)
+        return bfail(b, KQ_ERR_CUDA, hs[i]->err);
+    }
+    if (cudaStreamSynchronize(s) != cudaSuccess) return bfail(b, KQ_ERR_CUDA, "batch update");
+    std::vector<int> reasm;
+    for (int i : act) {
+      assemble_finish(hs[i], &n2, nullptr);
+      const double rn = std::sqrt(n2);
+      if (!(rn == rn)) return bfail(b, KQ_ERR_NUMERIC, "residual NaN in QP " + std::to_string(i));
+      iters[i] = it;
+      if (rn < mu[i]) {
+        if (mu[i] < o.mu_tol) {
+          done[i] = 1;
+          stat[i] = KQ_OK;
+          hs[i]->solved = true;
+          continue;
+        }
+        ++kexp[i];
+        mu[i] = o.mu0 * std::pow(10.0, -(double)kexp[i]);
+        hs[i]->mu = mu[i];
+        reasm.push_back(i);
+      }
+    }
+    for (int i : reasm)
+      if (assemble_enqueue(hs[i]) != KQ_OK) return bfail(b, KQ_ERR_CUDA, hs[i]->err);
+    if (!reasm.empty()) {
+      if (cudaStreamSynchronize(s) != cudaSuccess) return bfail(b, KQ_ERR_CUDA, "batch reassemble");
+      for (int i : reasm) assemble_finish(hs[i], &n2, nullptr);
+    }
+  }
+  for (int i = 0; i < nq; ++i) {
+    if (x && x[i]) outputs_enqueue(hs[i], x[i], nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (status) status[i] = stat[i];
+    st.ipm_iters_max = std::max(st.ipm_iters_max, iters[i]);
+    st.ipm_iters_total += iters[i];
+    if (stat[i] == KQ_OK) st.converged++;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return bfail(b, KQ_ERR_CUDA, "batch outputs");
+  st.pcg_kernel_ms = kernel_ms;
+  st.pcg_launches = b->B.launches;
+  st.time_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
+  return st.converged == nq ? KQ_OK : KQ_ERR_IPM_MAXIT;
+}
+
+}  // extern "C"

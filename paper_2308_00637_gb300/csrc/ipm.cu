@@ -464,10 +464,10 @@ __global__ void k_update(DevProb P, DevState S, const double *z, const double *d
     S.le[e] += al * z[P.n + e];
 }
 
-__global__ void k_reduce_cols(int nb, int ncol, const double *part, const int *is_min, double *out) {
+__global__ void k_reduce_cols(int nb, int ncol, const double *part, int min_mask, double *out) {
   __shared__ double sh[32];
   for (int c = 0; c < ncol; ++c) {
-    if (is_min[c]) {
+    if ((min_mask >> c) & 1) {
       double v = INFINITY;
       for (int i = threadIdx.x; i < nb; i += blockDim.x) v = fmin(v, part[c * nb + i]);
       v = block_min(v, sh);
@@ -583,15 +583,25 @@ kq_status hx_apply(kq_problem *h, const double *v, double *hx) {
   return KQ_OK;
 }
 
-kq_status fetch(kq_problem *h, int ncols, std::vector<int> mins, double *out) {
-  int flags[8] = {0};
-  for (size_t i = 0; i < mins.size(); ++i) flags[i] = mins[i];
-  int *hf = reinterpret_cast<int *>(h->h_red + 32);
-  memcpy(hf, flags, sizeof flags);
-  KQ_CUDA(h, cudaMemcpyAsync(h->dflags, hf, 8 * sizeof(int), cudaMemcpyHostToDevice, h->stream));
-  k_reduce_cols<<<1, 256, 0, h->stream>>>(NB, ncols, h->red, h->dflags, h->red_out);
+}  // namespace
+
+// Reduce ncols columns of block partials (sum, or min where bit c of min_mask
+// is set) into h->h_red[off .. off+ncols) asynchronously (no host sync).
+kq_status reduce_async(kq_problem *h, int ncols, int min_mask, int off) {
+  k_reduce_cols<<<1, 256, 0, h->stream>>>(NB, ncols, h->red, min_mask, h->red_out + off);
   ++h->launches;
-  KQ_CUDA(h, cudaMemcpyAsync(h->h_red, h->red_out, ncols * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  KQ_CUDA(h, cudaMemcpyAsync(h->h_red + off, h->red_out + off, ncols * sizeof(double),
+                             cudaMemcpyDeviceToHost, h->stream));
+  return KQ_OK;
+}
+
+namespace {
+
+kq_status fetch(kq_problem *h, int ncols, std::vector<int> mins, double *out) {
+  int mask = 0;
+  for (size_t i = 0; i < mins.size(); ++i) mask |= (mins[i] ? 1 : 0) << i;
+  kq_status rc = reduce_async(h, ncols, mask, 0);
+  if (rc != KQ_OK) return rc;
   KQ_CUDA(h, cudaStreamSynchronize(h->stream));
   for (int c = 0; c < ncols; ++c) out[c] = h->h_red[c];
   return KQ_OK;
@@ -599,6 +609,8 @@ kq_status fetch(kq_problem *h, int ncols, std::vector<int> mins, double *out) {
 
 // initial point of the iteration (x0 from the bounds, slacks max(value, 1),
 // inequality multipliers 1, lam_e 0)
+}  // namespace
+
 kq_status init_state(kq_problem *h) {
   k_init_x<<<NB, NT, 0, h->stream>>>(h->P, h->S);
   ++h->launches;
@@ -613,8 +625,6 @@ kq_status init_state(kq_problem *h) {
   return KQ_OK;
 }
 
-}  // namespace
-
 kq_status kq_fail(kq_problem *h, kq_status st, const std::string &msg) {
   if (h) h->err = msg;
   else g_global_err = msg;
@@ -624,7 +634,7 @@ kq_status kq_fail(kq_problem *h, kq_status st, const std::string &msg) {
 // Residuals, D, dg, doubly augmented rhs and Jacobi diagonal at (state, mu).
 // Returns the squared residual norm pieces through h->h_red: [0] = |r|^2,
 // [1] = |r_H|^2.
-static kq_status assemble_norms(kq_problem *h, double *norm2, double *rH2) {
+kq_status assemble_enqueue(kq_problem *h) {
   const DevProb &P = h->P;
   h->K.mu = h->mu;
   kq_status st;
@@ -650,14 +660,98 @@ static kq_status assemble_norms(kq_problem *h, double *norm2, double *rH2) {
   k_x_resid<<<NB, NT, 0, h->stream>>>(P, h->S, h->K, h->hx, h->acc1, h->acc2, h->acc3, h->red);
   ++h->launches;
   KQ_CUDA(h, cudaGetLastError());
-  double out[3];
-  kq_status rc = fetch(h, 3, {0, 0, 0}, out);
-  if (rc != KQ_OK) return rc;
-  *norm2 = out[0] + out[2];
-  if (rH2) *rH2 = out[1];
+  return reduce_async(h, 3, 0, 0);
+}
+
+// after a stream synchronisation: |r|^2 (all blocks of Eq. (7)) and |r_H|^2
+void assemble_finish(kq_problem *h, double *norm2, double *rH2) {
+  *norm2 = h->h_red[0] + h->h_red[2];
+  if (rH2) *rH2 = h->h_red[1];
   h->kkt_valid = true;
+}
+
+static kq_status assemble_norms(kq_problem *h, double *norm2, double *rH2) {
+  kq_status rc = assemble_enqueue(h);
+  if (rc != KQ_OK) return rc;
+  KQ_CUDA(h, cudaStreamSynchronize(h->stream));
+  assemble_finish(h, norm2, rH2);
   return KQ_OK;
 }
+
+// step recovery and ratio-test reductions for the direction in h->z
+kq_status recover_enqueue(kq_problem *h) {
+  kq_status rc = rowdot(h, h->z, h->t, h->tC);
+  if (rc != KQ_OK) return rc;
+  k_recover_ratio<<<NB, NT, 0, h->stream>>>(h->P, h->S, h->K, h->z, h->t, h->dsl, h->dsu, h->dslx,
+                                             h->dsux, h->dllx, h->dlux, h->red);
+  ++h->launches;
+  return reduce_async(h, 2, 3, 4);
+}
+
+void recover_finish(kq_problem *h, double gamma, double *ax, double *al) {
+  *ax = std::min(1.0, gamma * h->h_red[4]);
+  *al = std::min(1.0, gamma * h->h_red[5]);
+}
+
+kq_status update_enqueue(kq_problem *h, double ax, double al) {
+  k_update<<<NB, NT, 0, h->stream>>>(h->P, h->S, h->z, h->dsl, h->dsu, h->dslx, h->dsux, h->dllx,
+                                      h->dlux, ax, al);
+  ++h->launches;
+  KQ_CUDA(h, cudaGetLastError());
+  return KQ_OK;
+}
+
+// x and the multipliers in original units into caller buffers (async)
+kq_status outputs_enqueue(kq_problem *h, double *x, double *lam_lA, double *lam_uA,
+                          double *lam_lx, double *lam_ux, double *lam_e) {
+  const size_t nb = h->n * 8;
+  if (x) KQ_CUDA(h, cudaMemcpyAsync(x, h->S.x, nb, cudaMemcpyDefault, h->stream));
+  if (lam_lA || lam_uA || lam_lx || lam_ux || lam_e) {
+    double *olA = h->tmp + h->n + h->me, *ouA = h->tmp + h->n + h->me + h->m, *olx = h->acc2,
+           *oux = h->acc3, *oe = h->tmp + h->n;
+    k_unscale<<<NB, NT, 0, h->stream>>>(h->P, h->S, h->sigma, h->rhoC, olA, ouA, olx, oux, oe);
+    ++h->launches;
+    if (lam_lA && h->m) KQ_CUDA(h, cudaMemcpyAsync(lam_lA, olA, h->m * 8, cudaMemcpyDefault, h->stream));
+    if (lam_uA && h->m) KQ_CUDA(h, cudaMemcpyAsync(lam_uA, ouA, h->m * 8, cudaMemcpyDefault, h->stream));
+    if (lam_lx) KQ_CUDA(h, cudaMemcpyAsync(lam_lx, olx, nb, cudaMemcpyDefault, h->stream));
+    if (lam_ux) KQ_CUDA(h, cudaMemcpyAsync(lam_ux, oux, nb, cudaMemcpyDefault, h->stream));
+    if (lam_e && h->me) KQ_CUDA(h, cudaMemcpyAsync(lam_e, oe, h->me * 8, cudaMemcpyDefault, h->stream));
+    h->kkt_valid = false;
+  }
+  return KQ_OK;
+}
+
+// small vector helpers used by the batched solver
+__global__ void k_vec_add(int64_t N, double *z, const double *dz) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    z[i] += dz[i];
+}
+__global__ void k_vec_resid(int64_t N, const double *rhs, const double *kz, double *res, double *part) {
+  __shared__ double sh[32];
+  double s[1] = {0.0};
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = rhs[i] - kz[i];
+    res[i] = v;
+    s[0] += v * v;
+  }
+  block_sum<1>(s, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+kq_status vec_add_enqueue(kq_problem *h, double *z, const double *dz) {
+  const int nb = (int)std::min<int64_t>(NB, ceil_div64(h->nkp, NT));
+  k_vec_add<<<nb, NT, 0, h->stream>>>(h->nkp, z, dz);
+  ++h->launches;
+  return KQ_OK;
+}
+// res = rhs - kz and |res|^2 into h->h_red[8] (async)
+kq_status vec_resid_enqueue(kq_problem *h, const double *rhs, const double *kz, double *res) {
+  KQ_CUDA(h, cudaMemsetAsync(h->red, 0, NB * sizeof(double), h->stream));
+  const int nb = (int)std::min<int64_t>(NB, ceil_div64(h->nkp, NT));
+  k_vec_resid<<<nb, NT, 0, h->stream>>>(h->nkp, rhs, kz, res, h->red);
+  ++h->launches;
+  return reduce_async(h, 1, 0, 8);
+}
+
 
 kq_status kkt_assemble(kq_problem *h) {
   double n2;
@@ -1074,16 +1168,12 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
     if (rc == KQ_WARN_PCG_MAXIT) st.pcg_maxit_hits++;
     else if (rc != KQ_OK) { final = rc; break; }
     // step recovery (A dx) and ratio test
-    if ((rc = rowdot(h, h->z, h->t, h->tC)) != KQ_OK) { final = rc; break; }
-    k_recover_ratio<<<NB, NT, 0, h->stream>>>(P, h->S, h->K, h->z, h->t, h->dsl, h->dsu, h->dslx,
-                                               h->dsux, h->dllx, h->dlux, h->red);
-    double mins[2];
-    if ((rc = fetch(h, 2, {1, 1}, mins)) != KQ_OK) { final = rc; break; }
-    const double ax = std::min(1.0, o.gamma * mins[0]);
-    const double al = std::min(1.0, o.gamma * mins[1]);
+    if ((rc = recover_enqueue(h)) != KQ_OK) { final = rc; break; }
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) { final = kq_fail(h, KQ_ERR_CUDA, "sync"); break; }
+    double ax, al;
+    recover_finish(h, o.gamma, &ax, &al);
     if (!(ax == ax) || !(al == al)) { final = kq_fail(h, KQ_ERR_NUMERIC, "NaN step length"); break; }
-    k_update<<<NB, NT, 0, h->stream>>>(P, h->S, h->z, h->dsl, h->dsu, h->dslx, h->dsux, h->dllx,
-                                        h->dlux, ax, al);
+    if ((rc = update_enqueue(h, ax, al)) != KQ_OK) { final = rc; break; }
     if ((rc = assemble_norms(h, &n2, nullptr)) != KQ_OK) { final = rc; break; }
     const double rn = sqrt(n2);
     if (!(rn == rn)) { final = kq_fail(h, KQ_ERR_NUMERIC, "residual norm is NaN"); break; }

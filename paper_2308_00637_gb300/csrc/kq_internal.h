@@ -192,5 +192,38 @@ kq_status pcg_dense_raw(const DevProb &P, const double *Dl, const double *Du, co
                         double timeout_s, cudaStream_t stream, int *iters, double *rr,
                         double *bb, std::string *msg);
 
+// batched dense PCG (pcg.cu)
+struct BatchPcg {
+  int nqp = 0, G = 0, max_n = 0;
+  std::vector<void *> allocs;
+  unsigned char *args = nullptr, *teams = nullptr;
+  int *cta_team = nullptr, *team_qps = nullptr;
+  int *d_iters = nullptr, *d_err = nullptr;
+  double *d_resn = nullptr;
+  unsigned char *h_status = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  long long launches = 0;
+};
+kq_status batch_pcg_setup(BatchPcg &B, int nqp, int sms, int max_n, std::string &err);
+void batch_pcg_free(BatchPcg &B);
+kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
+                           const std::vector<int> &idx, const std::vector<const double *> &rhs,
+                           const std::vector<double *> &out, const std::vector<double> &tol,
+                           const std::vector<int> &maxit, int apply, int prec, cudaStream_t s,
+                           std::vector<int> &iters, std::vector<int> &errs,
+                           std::vector<double> &rr, std::vector<double> &bb, float *ms,
+                           std::string &err, const std::vector<double> *weight = nullptr);
+
 // ipm kernels (ipm.cu)
 kq_status kkt_assemble(kq_problem *h);   // residuals, rhs, D, diag at state & mu
+kq_status init_state(kq_problem *h);
+kq_status reduce_async(kq_problem *h, int ncols, int min_mask, int off);
+kq_status assemble_enqueue(kq_problem *h);                      // -> h_red[0..2]
+void assemble_finish(kq_problem *h, double *norm2, double *rH2);
+kq_status recover_enqueue(kq_problem *h);                       // -> h_red[4..5]
+void recover_finish(kq_problem *h, double gamma, double *ax, double *al);
+kq_status update_enqueue(kq_problem *h, double ax, double al);
+kq_status outputs_enqueue(kq_problem *h, double *x, double *lam_lA, double *lam_uA,
+                          double *lam_lx, double *lam_ux, double *lam_e);
+kq_status vec_add_enqueue(kq_problem *h, double *z, const double *dz);
+kq_status vec_resid_enqueue(kq_problem *h, const double *rhs, const double *kz, double *res);  // -> h_red[8]

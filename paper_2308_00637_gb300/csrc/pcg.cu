@@ -200,10 +200,12 @@ struct OpCsr {
 // ---------------------------------------------------------------- DENSE (explicit H, dense A, C)
 template <class HS, class AS>
 struct OpDense {
+  // vcta / vG: this CTA's rank and the number of CTAs working on the problem
+  // (the whole grid for a single problem, a team in the batched solver)
   template <class T>
   static __device__ double phaseA(const PcgArgs &a, const double *ysrc, const double *pold,
                                   double *pnew, double beta, int64_t vb, int64_t ve,
-                                  unsigned char *smem) {
+                                  unsigned char *smem, int vcta, int vG) {
     const DevProb &P = a.P;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = blockDim.x >> 5;
@@ -220,7 +222,7 @@ struct OpDense {
     const HS *Hd = reinterpret_cast<const HS *>(P.Hd);
     const AS *Ad = reinterpret_cast<const AS *>(P.Ad);
     const int64_t R = n + m + me;
-    const int64_t gw0 = (int64_t)blockIdx.x * nw + warp, GW = (int64_t)gridDim.x * nw;
+    const int64_t gw0 = (int64_t)vcta * nw + warp, GW = (int64_t)vG * nw;
     const int64_t lo_off = n + me, up_off = n + me + m;
     for (int64_t row = gw0; row < R; row += GW) {
       if (row < n) {
@@ -797,7 +799,7 @@ template <class OP, class T>
 __device__ __forceinline__ double run_phaseA(const PcgArgs &a, const double *ysrc,
                                              const double *pold, double *pnew, double beta,
                                              int64_t vb, int64_t ve, unsigned char *smem,
-                                             PipeState &ps, bool &ok) {
+                                             PipeState &ps, bool &ok, int vcta, int vG) {
   if constexpr (IsLowrank<OP>::value) {
     return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ok);
   } else if constexpr (IsStaged<OP>::value) {
@@ -805,15 +807,16 @@ __device__ __forceinline__ double run_phaseA(const PcgArgs &a, const double *ysr
     return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ps, ok);
   } else {
     ok = true;
-    return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem);
+    return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, vcta, vG);
   }
 }
 
+// The PCG solve (or one product in APPLY mode) of one problem by the CTAs
+// cta = 0..G-1 (the whole grid, or one team of the batched solver).
 template <class OP, class T>
-__global__ void __launch_bounds__(512, 1) pcg_kernel(PcgArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double sh[32 * 2];
-  const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+__device__ void pcg_body(const PcgArgs &a, const int cta, const int G, unsigned char *smem,
+                         double *sh) {
+  const int tid = threadIdx.x;
   const int64_t nkp = a.P.nkp, n = a.P.n;
   const int64_t chunk = ceil_div64(nkp, G);
   const int64_t vb = min(nkp, (int64_t)cta * chunk), ve = min(nkp, vb + chunk);
@@ -856,7 +859,7 @@ __global__ void __launch_bounds__(512, 1) pcg_kernel(PcgArgs a) {
   while (ok) {
     if (!a.apply && (rr <= a.tol2 * bb || it >= a.maxit)) break;
     // ---- phase A: q = K p,  p = y + beta p_old
-    double pq = run_phaseA<OP, T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ps, ok);
+    double pq = run_phaseA<OP, T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ps, ok, cta, G);
     if (!ok) break;
     {
       double v1[1] = {pq};
@@ -915,6 +918,33 @@ __global__ void __launch_bounds__(512, 1) pcg_kernel(PcgArgs a) {
     *a.iters = it;
     a.resn[0] = rr;
     a.resn[1] = bb;
+  }
+}
+
+template <class OP, class T>
+__global__ void __launch_bounds__(512, 1) pcg_kernel(PcgArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sh[32 * 2];
+  pcg_body<OP, T>(a, blockIdx.x, gridDim.x, smem, sh);
+}
+
+// Batched dense PCG: CTA b belongs to team cta_team[b]; a team works through
+// its list of problems one after another, each with pcg_body on the team's
+// CTAs (team-local bounded barrier in that problem's GridBar).
+struct TeamInfo { int first_cta, size, qp_begin, qp_end; };
+
+template <class HS, class AS, class T>
+__global__ void __launch_bounds__(512, 1) pcg_batch_kernel(const PcgArgs *__restrict__ args,
+                                                            const int *__restrict__ cta_team,
+                                                            const TeamInfo *__restrict__ teams,
+                                                            const int *__restrict__ team_qps) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sh[32 * 2];
+  const TeamInfo ti = teams[cta_team[blockIdx.x]];
+  const int rank = blockIdx.x - ti.first_cta;
+  for (int q = ti.qp_begin; q < ti.qp_end; ++q) {
+    pcg_body<OpDense<HS, AS>, T>(args[team_qps[q]], rank, ti.size, smem, sh);
+    __syncthreads();
   }
 }
 
@@ -1120,6 +1150,209 @@ kq_status pcg_dense_raw(const DevProb &P, const double *Dl, const double *Du, co
   if (hs[0] == 4) { if (msg) *msg = "p'Kp <= 0 (K not positive definite)"; return KQ_ERR_NOT_CONVEX; }
   if (hs[0] == 8) { if (msg) *msg = "NaN in PCG"; return KQ_ERR_NUMERIC; }
   if (hs[0] != 0) { if (msg) *msg = "PCG error flag"; return KQ_ERR_CUDA; }
+  return KQ_OK;
+}
+
+// ---------------------------------------------------------------- batched dense PCG
+namespace {
+template <class X> X *balloc(std::vector<void *> &allocs, size_t count) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, std::max<size_t>(count, 1) * sizeof(X)) != cudaSuccess) return nullptr;
+  allocs.push_back(p);
+  return reinterpret_cast<X *>(p);
+}
+}  // namespace
+
+kq_status batch_pcg_setup(BatchPcg &B, int nqp, int sms, int max_n, std::string &err) {
+  B.nqp = nqp;
+  B.G = sms;   // one CTA per SM (512 threads, ~100 registers each)
+  B.max_n = max_n;
+  B.args = balloc<unsigned char>(B.allocs, (size_t)nqp * sizeof(PcgArgs));
+  B.cta_team = balloc<int>(B.allocs, B.G);
+  B.teams = balloc<unsigned char>(B.allocs, (size_t)B.G * sizeof(TeamInfo));
+  B.team_qps = balloc<int>(B.allocs, nqp);
+  B.d_iters = balloc<int>(B.allocs, nqp);
+  B.d_err = balloc<int>(B.allocs, nqp);
+  B.d_resn = balloc<double>(B.allocs, 2 * (size_t)nqp);
+  if (!B.args || !B.cta_team || !B.teams || !B.team_qps || !B.d_iters || !B.d_err || !B.d_resn) {
+    err = "batch PCG work space";
+    return KQ_ERR_OOM;
+  }
+  if (cudaMallocHost((void **)&B.h_status, (size_t)nqp * (2 * sizeof(int) + 2 * sizeof(double))) != cudaSuccess) {
+    err = "batch pinned status";
+    return KQ_ERR_OOM;
+  }
+  if (cudaEventCreate(&B.ev0) != cudaSuccess || cudaEventCreate(&B.ev1) != cudaSuccess) {
+    err = "batch events";
+    return KQ_ERR_CUDA;
+  }
+  return KQ_OK;
+}
+
+void batch_pcg_free(BatchPcg &B) {
+  for (void *p : B.allocs) cudaFree(p);
+  B.allocs.clear();
+  if (B.h_status) cudaFreeHost(B.h_status);
+  B.h_status = nullptr;
+  if (B.ev0) cudaEventDestroy(B.ev0);
+  if (B.ev1) cudaEventDestroy(B.ev1);
+  B.ev0 = B.ev1 = nullptr;
+}
+
+// One launch: PCG solves (apply = 0) or single K*v products (apply = 1) of the
+// listed problems.  Teams: problems whose share of the total cost is worth
+// two or more CTAs get their own team of that size; the rest are packed onto
+// single-CTA teams, largest first onto the least-loaded team.
+kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
+                           const std::vector<int> &idx, const std::vector<const double *> &rhs,
+                           const std::vector<double *> &out, const std::vector<double> &tol,
+                           const std::vector<int> &maxit, int apply, int prec, cudaStream_t s,
+                           std::vector<int> &iters, std::vector<int> &errs,
+                           std::vector<double> &rr, std::vector<double> &bb, float *ms,
+                           std::string &err, const std::vector<double> *weight) {
+  const int k = (int)idx.size();
+  iters.assign(k, 0); errs.assign(k, 0); rr.assign(k, 0.0); bb.assign(k, 0.0);
+  if (k == 0) { if (ms) *ms = 0.f; return KQ_OK; }
+  // ---- costs: bytes per product times the expected number of products
+  std::vector<double> cost(k);
+  double total = 0.0;
+  for (int j = 0; j < k; ++j) {
+    const kq_problem *h = hs[idx[j]];
+    const double hb = h->P.hdtype == KQ_F64 ? 8.0 : (h->P.hdtype == KQ_F32 ? 4.0 : 2.0);
+    const double ab = h->P.adtype == KQ_F64 ? 8.0 : 4.0;
+    cost[j] = (hb * h->n * h->n + ab * h->m * h->n + 64.0 * h->nkp) *
+              (weight ? std::max(1.0, (*weight)[j]) : 1.0);
+    total += cost[j];
+  }
+  std::vector<int> order(k);
+  for (int j = 0; j < k; ++j) order[j] = j;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+  std::vector<TeamInfo> teams;
+  std::vector<std::vector<int>> members;
+  int used = 0;
+  const int G = B.G;
+  size_t q = 0;
+  for (; q < order.size(); ++q) {
+    const int j = order[q];
+    int t = (int)std::floor(G * cost[j] / total);
+    t = std::min(t, hs[idx[j]]->W.G);
+    if (t < 2 || used + t > G - 1) break;
+    teams.push_back(TeamInfo{used, t, 0, 0});
+    members.push_back({j});
+    used += t;
+  }
+  const int nsingle = std::max(1, G - used);
+  const int first_single = (int)teams.size();
+  std::vector<double> load(nsingle, 0.0);
+  for (int c = 0; c < nsingle; ++c) {
+    teams.push_back(TeamInfo{used + c, 1, 0, 0});
+    members.push_back({});
+  }
+  for (; q < order.size(); ++q) {
+    const int j = order[q];
+    int best = 0;
+    for (int c = 1; c < nsingle; ++c) if (load[c] < load[best]) best = c;
+    load[best] += cost[j];
+    members[first_single + best].push_back(j);
+  }
+  const int nblocks = used + nsingle;
+  std::vector<int> cta_team(nblocks), team_qps;
+  for (size_t t = 0; t < teams.size(); ++t) {
+    teams[t].qp_begin = (int)team_qps.size();
+    for (int j : members[t]) team_qps.push_back(j);
+    teams[t].qp_end = (int)team_qps.size();
+    for (int c = 0; c < teams[t].size; ++c) cta_team[teams[t].first_cta + c] = (int)t;
+  }
+  // ---- per-problem arguments
+  std::vector<PcgArgs> args(k);
+  std::vector<int> team_of(k, 0);
+  for (size_t t = 0; t < teams.size(); ++t)
+    for (int j : members[t]) team_of[j] = (int)t;
+  size_t smem = 0;
+  for (int j = 0; j < k; ++j) {
+    kq_problem *h = hs[idx[j]];
+    PcgWork &W = h->W;
+    PcgArgs &a = args[j];
+    a = PcgArgs{};
+    a.P = h->P;
+    a.Dl = h->K.Dl; a.Du = h->K.Du; a.cl = h->K.cl; a.cu = h->K.cu;
+    a.dg = h->K.dg; a.diag = h->K.diag; a.mu = h->K.mu;
+    a.rhs = rhs[j]; a.z = out[j];
+    a.r = W.r; a.y = W.y; a.pb0 = W.pb0; a.pb1 = W.pb1; a.qlam = W.qlam;
+    a.accx = prec == KQ_PREC_MIXED ? (void *)W.accx32 : (void *)W.accx64;
+    a.g = nullptr; a.slots = W.slots;
+    a.win_cap = (int)h->n;
+    a.bar.count = W.bar; a.bar.gen = W.bar + 1; a.bar.err = B.d_err + j;
+    a.bar.nblocks = (unsigned)teams[team_of[j]].size;
+    a.bar.budget_ns = (uint64_t)(h->timeout_s * 1e9);
+    a.tol2 = tol[j] * tol[j]; a.maxit = maxit[j]; a.apply = apply;
+    a.iters = B.d_iters + j; a.resn = B.d_resn + 2 * j;
+    a.stages = 2; a.producer = 0; a.copy_piece = 16;
+    smem = std::max(smem, (size_t)2 * h->n * (prec == KQ_PREC_MIXED ? sizeof(float) : sizeof(double)));
+    if (cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) { err = "memset"; return KQ_ERR_CUDA; }
+  }
+  const kq_problem *h0 = hs[idx[0]];
+  for (int j = 1; j < k; ++j) {
+    const kq_problem *h = hs[idx[j]];
+    if (h->P.hdtype != h0->P.hdtype || h->P.adtype != h0->P.adtype || h->P.hkind != KQ_H_DENSE) {
+      err = "batched problems must share the dense H and A storage types";
+      return KQ_ERR_ARG;
+    }
+  }
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(B.d_err, 0, k * sizeof(int), s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(B.args, args.data(), k * sizeof(PcgArgs), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(B.cta_team, cta_team.data(), nblocks * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(B.teams, teams.data(), teams.size() * sizeof(TeamInfo), cudaMemcpyHostToDevice, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(B.team_qps, team_qps.data(), team_qps.size() * sizeof(int), cudaMemcpyHostToDevice, s)) != cudaSuccess) {
+    err = std::string("batch upload: ") + cudaGetErrorString(e);
+    return KQ_ERR_CUDA;
+  }
+  const void *f;
+  const bool mixed = prec == KQ_PREC_MIXED;
+  if (h0->P.hdtype == KQ_BF16 && h0->P.adtype == KQ_F32)
+    f = mixed ? (const void *)pcg_batch_kernel<__nv_bfloat16, float, float>
+              : (const void *)pcg_batch_kernel<__nv_bfloat16, float, double>;
+  else if (h0->P.hdtype == KQ_F64 && h0->P.adtype == KQ_F64)
+    f = mixed ? (const void *)pcg_batch_kernel<double, double, float>
+              : (const void *)pcg_batch_kernel<double, double, double>;
+  else {
+    err = "batched PCG supports bf16 H with f32 A, or f64 H with f64 A";
+    return KQ_ERR_ARG;
+  }
+  if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) {
+    err = std::string("batch attribute: ") + cudaGetErrorString(e);
+    return KQ_ERR_CUDA;
+  }
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 512, smem);
+  if (per_sm * B.G < nblocks) { err = "batched PCG grid does not fit"; return KQ_ERR_ARG; }
+  const PcgArgs *pa = reinterpret_cast<const PcgArgs *>(B.args);
+  const TeamInfo *pt = reinterpret_cast<const TeamInfo *>(B.teams);
+  void *kargs[] = {(void *)&pa, (void *)&B.cta_team, (void *)&pt, (void *)&B.team_qps};
+  cudaEventRecord(B.ev0, s);
+  if ((e = cudaLaunchCooperativeKernel(f, dim3(nblocks), dim3(512), kargs, smem, s)) != cudaSuccess) {
+    err = std::string("batch launch: ") + cudaGetErrorString(e);
+    return KQ_ERR_CUDA;
+  }
+  cudaEventRecord(B.ev1, s);
+  B.launches++;
+  int *hi = reinterpret_cast<int *>(B.h_status);
+  int *he = hi + B.nqp;
+  double *hr = reinterpret_cast<double *>(he + B.nqp);
+  if ((e = cudaMemcpyAsync(hi, B.d_iters, k * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(he, B.d_err, k * sizeof(int), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(hr, B.d_resn, 2 * k * sizeof(double), cudaMemcpyDeviceToHost, s)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(s)) != cudaSuccess) {
+    err = std::string("batch status: ") + cudaGetErrorString(e);
+    return KQ_ERR_CUDA;
+  }
+  float t = 0.f;
+  cudaEventElapsedTime(&t, B.ev0, B.ev1);
+  if (ms) *ms = t;
+  for (int j = 0; j < k; ++j) {
+    iters[j] = hi[j]; errs[j] = he[j]; rr[j] = hr[2 * j]; bb[j] = hr[2 * j + 1];
+  }
   return KQ_OK;
 }
 

@@ -81,6 +81,8 @@ class QPData:
     def H_dense(self) -> np.ndarray:
         """Explicit H in float64 (only for sizes where that is affordable)."""
         if self.hkind == "dense":
+            if self.H is None:
+                return from_bf16_bits(self.meta["H_bf16_bits"]).reshape(self.n, self.n)
             return np.asarray(self.H, dtype=np.float64)
         if self.hkind == "csr_lsq":
             P = self.P.astype(np.float64)
@@ -91,7 +93,7 @@ class QPData:
     def objective(self, x: np.ndarray) -> float:
         """1/2 x^T H x + p^T x, evaluated from the operator's structure."""
         if self.hkind == "dense":
-            Hx = np.asarray(self.H, dtype=np.float64) @ x
+            Hx = self.H_dense() @ x
         elif self.hkind == "csr_lsq":
             P = self.P.astype(np.float64)
             Hx = 2.0 * (P.T @ (self.w * (P @ x)))
@@ -129,7 +131,9 @@ def from_bf16_bits(bits: np.ndarray) -> np.ndarray:
 # constraints A x >= b, -1 <= x <= 1.  Draw order: Q, p, A, x0, u.
 # ---------------------------------------------------------------------------
 def dense_qp(n: int = 200, m: int = 100, q: Optional[int] = None, seed: int = 0,
-             h_bf16: bool = False, a_f32: bool = False) -> QPData:
+             h_bf16: bool = False, a_f32: bool = False, light: bool = False) -> QPData:
+    """``light`` (with h_bf16 and a_f32): keep only the bf16 bits of H and A in
+    float32 (no float64 copies); H_dense() / A_matrix() rebuild them."""
     rng = np.random.default_rng(seed)
     q = int(round(1.5 * n)) if q is None else q
     Q = rng.standard_normal((q, n))
@@ -139,13 +143,19 @@ def dense_qp(n: int = 200, m: int = 100, q: Optional[int] = None, seed: int = 0,
     u = rng.uniform(0.1, 1.0, m)
     H = Q.T @ Q / q + 1e-2 * np.eye(n)
     H = 0.5 * (H + H.T)
+    del Q
     meta = {"seed": seed, "q": q, "a_f32": a_f32}
     if h_bf16:
-        bits = to_bf16_bits(H)
-        H = from_bf16_bits(bits).reshape(n, n)
-        meta["H_bf16_bits"] = bits.reshape(n, n)
+        bits = to_bf16_bits(H).reshape(n, n)
+        H = None if light else from_bf16_bits(bits).reshape(n, n)
+        meta["H_bf16_bits"] = bits
     if a_f32:
-        A = A.astype(np.float32).astype(np.float64)
+        A = A.astype(np.float32)
+        b = A.astype(np.float64) @ x0 - u
+        if not light:
+            A = A.astype(np.float64)
+        return QPData(n=n, hkind="dense", p=p, H=H, akind="dense", A=A,
+                      lA=b, uA=_full(m, INF), lx=_full(n, -1.0), ux=_full(n, 1.0), meta=meta)
     b = A @ x0 - u
     return QPData(n=n, hkind="dense", p=p, H=H, akind="dense", A=A,
                   lA=b, uA=_full(m, INF), lx=_full(n, -1.0), ux=_full(n, 1.0),
@@ -302,12 +312,13 @@ def batch_sizes(nqp: int = 512, lo: int = 64, hi: int = 4096, size_seed: int = 0
     return [int(max(2, 2 * round(np.exp(v) / 2))) for v in u]
 
 
-def batch_qp(k: int, n: int) -> QPData:
-    return dense_qp(n, n // 2, q=(3 * n) // 2, seed=k + 1, h_bf16=True, a_f32=True)
+def batch_qp(k: int, n: int, light: bool = False) -> QPData:
+    return dense_qp(n, n // 2, q=(3 * n) // 2, seed=k + 1, h_bf16=True, a_f32=True, light=light)
 
 
-def config3(nqp: int = 512, lo: int = 64, hi: int = 4096) -> List[QPData]:
-    return [batch_qp(k, n) for k, n in enumerate(batch_sizes(nqp, lo, hi))]
+def config3(nqp: int = 512, lo: int = 64, hi: int = 4096, light: bool = True) -> List[QPData]:
+    """512 dense QPs; ``light`` keeps H as bf16 bits and A as float32 only."""
+    return [batch_qp(k, n, light) for k, n in enumerate(batch_sizes(nqp, lo, hi))]
 
 
 def tiny_qp(n: int, m: int, seed: int, me: int = 0, two_sided: bool = True,

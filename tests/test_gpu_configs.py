@@ -1,0 +1,71 @@
+"""Parity at the workloads' full sizes (GPU).
+
+* c0 (n = 200) and c2 (linear SVM, 50k samples) and c4 (dose QP at 1/4 size):
+  the oracle's full FP64 solve (LDL^T, Woodbury, banded Cholesky) against the
+  GPU solve, both precisions: objective within 1e-6 relative, KKT_rel <= 1e-6,
+  complementarity of the oracle's size.
+* c1 (dose QP, 2e7 nnz, the benchmark workload): properties that hold at any
+  size -- KKT_rel <= 1e-6 evaluated by the oracle's metric code in FP64 from
+  the original data, mu_final = 1e-7, and the mixed and FP64 solutions agree
+  on the objective to 1e-6.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import qpgen
+from oracle.metrics import full_multipliers
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def kq():
+    import __graft_entry__ as g
+    g.build()
+    import paper_2308_00637_gb300 as m
+    m.load()
+    return m
+
+
+def _metrics(qp, out):
+    return oracle.kkt_metrics(qp, out["x"], out["lam_lA"], out["lam_uA"], out["lam_lx"],
+                              out["lam_ux"], out["lam_e"])
+
+
+@pytest.mark.parametrize("name", ["c0", "c2", "c4"])
+def test_config_against_oracle(kq, name):
+    qp = {"c0": qpgen.config0, "c2": qpgen.config2, "c4": qpgen.config4}[name]()
+    # the SVM dual: with sigma ~ 1/450, mu_tol = 1e-6 in scaled units leaves a
+    # duality gap of ~4.5 (objective ~1.03), and points passing |r| < mu differ
+    # by ~1e-4 in objective; both solvers stop at mu_tol = 1e-9 here instead
+    mu_tol = 1e-9 if name == "c2" else 1e-6
+    res = oracle.ipm_solve(qp, mu_tol=mu_tol)
+    assert res.status == "converged"
+    ref = oracle.kkt_metrics(qp, res.x, *full_multipliers(res.scaled, res.lam, qp))
+    f_ref = ref["objective"]
+    for prec in (0, 1):
+        rc, st, out = kq.solve(qp, kq.default_ipm_opts(precision=prec, mu_tol=mu_tol))
+        met = _metrics(qp, out)
+        print(name, "prec", prec, "ipm", st.ipm_iters, "pcg", st.pcg_iters, "time %.3f" % st.time_s,
+              "kkt %.2e" % met["kkt_rel"], "df %.2e" % (abs(met["objective"] - f_ref) / (1 + abs(f_ref))))
+        assert abs(met["objective"] - f_ref) <= 1e-6 * (1 + abs(f_ref))
+        assert met["kkt_rel"] <= 1e-6
+        assert met["compl_rel"] <= 2.0 * ref["compl_rel"] + 1e-12
+        assert st.mu_final == pytest.approx(res.mu)
+
+
+def test_config1_properties(kq):
+    qp = qpgen.config1()
+    objs = []
+    for prec in (1, 0):
+        rc, st, out = kq.solve(qp, kq.default_ipm_opts(precision=prec))
+        met = _metrics(qp, out)
+        print("c1 prec", prec, "ipm", st.ipm_iters, "pcg", st.pcg_iters, "time %.3f" % st.time_s,
+              "kkt %.2e compl %.2e" % (met["kkt_rel"], met["compl_rel"]))
+        assert rc == kq.KQ_OK and st.mu_final == pytest.approx(1e-7)
+        assert met["kkt_rel"] <= 1e-6
+        # x >= 0 and the dose limits hold to the primal tolerance
+        assert np.min(out["x"]) >= -1e-9
+        objs.append(met["objective"])
+    assert abs(objs[0] - objs[1]) <= 1e-6 * (1 + abs(objs[1]))
