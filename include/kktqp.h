@@ -118,6 +118,7 @@ typedef struct {
   long long pcg_launches;  /* persistent PCG kernel launches                    */
   long long pcg_products;  /* K*v products inside PCG kernels (iterations+applies)*/
   long long kernel_launches; /* all kernels this call launched                   */
+  long long pcg_iters_f64; /* MIXED: PCG iterations run in FP64 (rescue passes) */
 } kq_ipm_stats;
 
 typedef struct {
@@ -134,6 +135,7 @@ typedef struct {
   int passes;              /* correction solves (1 unless refinement ran)       */
   double rel_res;          /* true ||rhs - K z|| / ||rhs|| in FP64              */
   double kernel_ms;        /* device time of the persistent kernels             */
+  int iters_f64;           /* iterations of FP64 passes (all of them in F64)    */
 } kq_pcg_stats;
 
 /* Fill *o with the paper's settings (gamma 0.99, mu/10, mu_tol 1e-6, PCG tol

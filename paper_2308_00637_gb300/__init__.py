@@ -57,7 +57,8 @@ class KqIpmStats(C.Structure):
                 ("compl_inf", C.c_double), ("pcg_iters", C.c_longlong),
                 ("pcg_maxit_hits", C.c_int), ("time_s", C.c_double), ("pcg_time_s", C.c_double),
                 ("pcg_kernel_ms", C.c_double), ("pcg_launches", C.c_longlong),
-                ("pcg_products", C.c_longlong), ("kernel_launches", C.c_longlong)]
+                ("pcg_products", C.c_longlong), ("kernel_launches", C.c_longlong),
+                ("pcg_iters_f64", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -70,7 +71,7 @@ class KqPcgOpts(C.Structure):
 
 class KqPcgStats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("passes", C.c_int),
-                ("rel_res", C.c_double), ("kernel_ms", C.c_double)]
+                ("rel_res", C.c_double), ("kernel_ms", C.c_double), ("iters_f64", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

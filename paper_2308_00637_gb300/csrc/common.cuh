@@ -89,45 +89,49 @@ __device__ __forceinline__ uint64_t global_ns() {
 }
 
 // ---------------------------------------------------------------- grid barrier
-// Sense-reversing barrier over all CTAs of a cooperative launch.  Every wait
-// is bounded by `budget_ns`; on expiry the CTA records KQ_ERR_TIMEOUT-style
-// status in *err and returns false (the caller then leaves its loop).  The
-// kernel is launched with cudaLaunchCooperativeKernel, so all CTAs are
-// co-resident and a correct program never reaches the budget.
+// Barrier over all CTAs of a cooperative launch (or of one team of it).  The
+// arrival counter only grows: the CTA that adds to it at count c waits until
+// the counter reaches the next multiple of nblocks, so no CTA has to reset
+// it and one release-add plus acquire-loads make the whole handshake.  Every
+// wait is bounded by `budget_ns`; on expiry, or when another CTA has already
+// recorded an error, the CTA records KQ_ERR_TIMEOUT-style status in *err and
+// returns false (the caller then leaves its loop).  The kernel is launched
+// with cudaLaunchCooperativeKernel, so all CTAs are co-resident and a
+// correct program never reaches the budget.  The counter is zeroed before
+// every launch.
 struct GridBar {
   unsigned int *count;   // arrival counter
-  unsigned int *gen;     // generation
+  unsigned int *gen;     // unused (kept for the layout of the status words)
   int *err;              // error flag (0 = ok)
   unsigned int nblocks;
   uint64_t budget_ns;
 };
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 
 __device__ __forceinline__ bool grid_sync(const GridBar &g) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    volatile unsigned int *vgen = g.gen;
-    unsigned int my = *vgen;
-    __threadfence();
-    unsigned int arrived = atomicAdd(g.count, 1u);
-    if (arrived == g.nblocks - 1) {
-      *g.count = 0;
-      __threadfence();
-      atomicAdd(g.gen, 1u);
-    } else {
-      uint64_t t0 = global_ns();
+    unsigned int old;
+    asm volatile("atom.add.release.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(g.count) : "memory");
+    const unsigned int target = (old / g.nblocks + 1u) * g.nblocks;
+    if ((int)(ld_acquire_u32(g.count) - target) < 0) {
+      const uint64_t t0 = global_ns();
       unsigned int spins = 0;
-      while (*vgen == my) {
+      while ((int)(ld_acquire_u32(g.count) - target) < 0) {
         if (((++spins) & 255u) == 0u) {
           if (global_ns() - t0 > g.budget_ns) { ok = 0; break; }
           if (*((volatile int *)g.err) != 0) { ok = 0; break; }
         }
       }
     }
-    __threadfence();
     if (!ok) atomicCAS(g.err, 0, 7 /* KQ_ERR_TIMEOUT */);
-    if (*((volatile int *)g.err) != 0) ok = 0;
     s_ok = ok;
   }
   __syncthreads();

@@ -31,9 +31,9 @@ __global__ void k_flags(int64_t N, const double *lo, const double *hi, uint8_t *
 }
 
 template <class HS>
-__global__ void k_dense_diag(int64_t n, const HS *H, double *d) {
+__global__ void k_dense_diag(int64_t n, int64_t ld, const HS *H, double *d) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    d[i] = ld_as_f64(H, i * n + i);
+    d[i] = ld_as_f64(H, i * ld + i);
 }
 
 template <class ZS>
@@ -66,13 +66,13 @@ __global__ void k_csr_diag(int64_t nP, const int64_t *rowptr, const int32_t *col
 
 // 1/||row||_2 of dense rows (or of the P rows selected by `rows`)
 template <class AS>
-__global__ void k_rho_dense(int64_t m, int64_t n, const AS *A, double *rho) {
+__global__ void k_rho_dense(int64_t m, int64_t n, int64_t ld, const AS *A, double *rho) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w0; i < m; i += W) {
     double s = 0.0;
-    for (int64_t c = lane; c < n; c += 32) { const double v = ld_as_f64(A, i * n + c); s += v * v; }
+    for (int64_t c = lane; c < n; c += 32) { const double v = ld_as_f64(A, i * ld + c); s += v * v; }
     s = warp_sum(s);
     if (lane == 0) rho[i] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
   }
@@ -183,7 +183,7 @@ __global__ void k_rowdot_dense(DevProb P, const double *v, double *t, double *tC
   for (int64_t i = w0; i < P.m + P.me; i += W) {
     double s = 0.0;
     if (i < P.m) {
-      for (int64_t c = lane; c < P.n; c += 32) s += ld_as_f64(A, i * P.n + c) * v[c];
+      for (int64_t c = lane; c < P.n; c += 32) s += ld_as_f64(A, i * P.ald + c) * v[c];
       s = warp_sum(s);
       if (lane == 0) t[i] = P.rhoA[i] * s;
     } else {
@@ -237,7 +237,7 @@ __global__ void k_hx_dense(DevProb P, const double *v, double *hx) {
   const HS *H = reinterpret_cast<const HS *>(P.Hd);
   for (int64_t i = w0; i < P.n; i += W) {
     double s = 0.0;
-    for (int64_t c = lane; c < P.n; c += 32) s += ld_as_f64(H, i * P.n + c) * v[c];
+    for (int64_t c = lane; c < P.n; c += 32) s += ld_as_f64(H, i * P.hld + c) * v[c];
     s = warp_sum(s);
     if (lane == 0) hx[i] = P.hscale * s;
   }
@@ -347,7 +347,7 @@ __global__ void k_rows_scatter_dense(DevProb P, RowCoef cf, double *acc1, double
     double s1 = 0.0, s2 = 0.0, s3 = 0.0;
     if (P.akind == KQ_A_DENSE) {
       for (int64_t a = 0; a < P.m; ++a) {
-        const double v = ld_as_f64(A, a * P.n + j);
+        const double v = ld_as_f64(A, a * P.ald + j);
         s1 += cf.c1[a] * v; s2 += cf.c2[a] * v; s3 += cf.c3[a] * v * v;
       }
     }
@@ -861,11 +861,16 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
   double *hdiag = dalloc<double>(h, n);
   if (!hdiag) return fail(KQ_ERR_OOM, "hdiag");
   if (H->kind == KQ_H_DENSE) {
-    P.Hd = up(H->val, (size_t)n * n * dtype_size(H->dtype));
+    // rows padded with zeros to a multiple of 8 entries (16-byte aligned rows)
+    P.hld = (n + 7) & ~(int64_t)7;
+    const size_t es = dtype_size(H->dtype);
+    P.Hd = up(nullptr, (size_t)n * P.hld * es);
     if (!P.Hd) return fail(KQ_ERR_OOM, "H");
-    if (H->dtype == KQ_F64) k_dense_diag<double><<<NB, NT, 0, s>>>(n, (const double *)P.Hd, hdiag);
-    else if (H->dtype == KQ_F32) k_dense_diag<float><<<NB, NT, 0, s>>>(n, (const float *)P.Hd, hdiag);
-    else k_dense_diag<__nv_bfloat16><<<NB, NT, 0, s>>>(n, (const __nv_bfloat16 *)P.Hd, hdiag);
+    if (cudaMemcpy2DAsync((void *)P.Hd, P.hld * es, H->val, n * es, n * es, n, cudaMemcpyDefault, s) != cudaSuccess)
+      return fail(KQ_ERR_CUDA, "H upload");
+    if (H->dtype == KQ_F64) k_dense_diag<double><<<NB, NT, 0, s>>>(n, P.hld, (const double *)P.Hd, hdiag);
+    else if (H->dtype == KQ_F32) k_dense_diag<float><<<NB, NT, 0, s>>>(n, P.hld, (const float *)P.Hd, hdiag);
+    else k_dense_diag<__nv_bfloat16><<<NB, NT, 0, s>>>(n, P.hld, (const __nv_bfloat16 *)P.Hd, hdiag);
   } else if (H->kind == KQ_H_LOWRANK) {
     P.k = H->cols;
     P.Z = up(H->val, (size_t)n * P.k * dtype_size(H->dtype));
@@ -943,10 +948,14 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
   uint8_t *hl = dalloc<uint8_t>(h, m), *hu = dalloc<uint8_t>(h, m);
   if (!rhoA || !lAd || !uAd || !hl || !hu) return fail(KQ_ERR_OOM, "A");
   if (akind == KQ_A_DENSE) {
-    P.Ad = up(A->val, (size_t)m * n * dtype_size(A->dtype));
+    P.ald = (n + 7) & ~(int64_t)7;
+    const size_t es = dtype_size(A->dtype);
+    P.Ad = up(nullptr, (size_t)m * P.ald * es);
     if (!P.Ad) return fail(KQ_ERR_OOM, "A values");
-    if (A->dtype == KQ_F64) k_rho_dense<double><<<NB, NT, 0, s>>>(m, n, (const double *)P.Ad, rhoA);
-    else k_rho_dense<float><<<NB, NT, 0, s>>>(m, n, (const float *)P.Ad, rhoA);
+    if (m > 0 && cudaMemcpy2DAsync((void *)P.Ad, P.ald * es, A->val, n * es, n * es, m, cudaMemcpyDefault, s) != cudaSuccess)
+      return fail(KQ_ERR_CUDA, "A upload");
+    if (A->dtype == KQ_F64) k_rho_dense<double><<<NB, NT, 0, s>>>(m, n, P.ald, (const double *)P.Ad, rhoA);
+    else k_rho_dense<float><<<NB, NT, 0, s>>>(m, n, P.ald, (const float *)P.Ad, rhoA);
   } else if (akind == KQ_A_ROWS_OF_P) {
     const int32_t *rows = P.arows;   // uploaded and checked with the CSR structure
     k_rho_rows<<<NB, NT, 0, s>>>(m, rows, P.rowptr, P.val, rhoA);
@@ -1165,6 +1174,7 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
     st.pcg_kernel_ms += ps.kernel_ms;
     st.pcg_launches += 2 * ps.passes;
     st.pcg_products += ps.iters + ps.passes;
+    st.pcg_iters_f64 += ps.iters_f64;
     if (rc == KQ_WARN_PCG_MAXIT) st.pcg_maxit_hits++;
     else if (rc != KQ_OK) { final = rc; break; }
     // step recovery (A dx) and ratio test

@@ -11,8 +11,10 @@ struct DevProb {
   int64_t n = 0, m = 0, me = 0, nkp = 0;
   int hkind = 0, hdtype = 0;
   double hscale = 1.0;               // sigma (DENSE, LOWRANK): H_scaled = hscale * H
-  // DENSE H (scaled by sigma), n x n row-major
+  // DENSE H (scaled by sigma), n x n row-major with leading dimension hld
+  // (rows padded with zeros to a multiple of 8 entries; 0 means n)
   const void *Hd = nullptr;
+  int64_t hld = 0, ald = 0;
   // CSR_LSQ: H = P' diag(w2) P, w2 = 2 sigma w
   int64_t nP = 0, nnz = 0;
   const int64_t *rowptr = nullptr;
@@ -68,6 +70,14 @@ struct DevKKT {
 //   sentinel {off = end of the last row}
 struct RowDesc { int32_t off; int32_t a; float w2hi; float w2lo; };
 struct ChunkInfo { int64_t src; int32_t nelem; int32_t desc0; int32_t ndesc; int32_t pad; };
+
+// Register-streamed CSR layout (FP32 products, rows of at most 128 nonzeros).
+// Each row's nonzeros are padded to a multiple of four and stored as groups
+// of four (one 16-byte load of values and one of window-relative columns per
+// lane); slot 4*l + q of a row belongs to lane l, load component q.  The host
+// permutes a row's nonzeros so that the 32 lanes of one component hit
+// distinct shared-memory banks where the row allows.
+struct RowSlot { int32_t off4; int32_t len4; int32_t a; float w2; };
 constexpr int KQ_MAX_STAGES = 8;
 
 // Shared-memory layout of the staged CSR kernel (byte offsets), identical on
@@ -112,6 +122,7 @@ struct PcgWork {
   double *accx64 = nullptr;    // n
   float *accx32 = nullptr;     // n
   double *g64 = nullptr;       // k + me (LOWRANK)
+  double *coefA = nullptr;     // m (DENSE column pass)
   double *slots = nullptr;     // 4 * G
   unsigned int *bar = nullptr; // [count, gen]
   int *err = nullptr;          // device error flag
@@ -123,6 +134,14 @@ struct PcgWork {
   int32_t *a_lo = nullptr, *a_hi = nullptr;
   int a_cap = 0, ch_cap = 0, desc_cap = 0, tab_cap = 0;
   int stages = 4, copy_piece = 16384, producer = 0;
+  // register-streamed CSR operator (FP32 products)
+  bool rows_ok = false;
+  RowSlot *rslot = nullptr;    // nP
+  float *rval = nullptr;       // 4 * sum(len4)
+  int32_t *rcol = nullptr;     // 4 * sum(len4), relative to the CTA's window start
+  int rws = 0;                 // stride of the per-warp accumulators (floats)
+  int pf_dist = 2;             // L2 prefetch distance in warp steps
+  size_t smem_rows = 0;
   int64_t *row_begin = nullptr;   // G+1 partition of rows (P rows / dense rows)
   int32_t *win_lo = nullptr, *win_hi = nullptr;  // G column windows (CSR)
   int *h_pinned = nullptr;     // pinned host mirror for status words

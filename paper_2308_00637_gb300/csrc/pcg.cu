@@ -56,6 +56,14 @@ struct PcgArgs {
   int copy_piece;               // bytes per bulk copy (multiple of 16)
   int stages;                   // shared-memory ring depth
   int producer;                 // 0: per-thread cp.async, 1: bulk copies + mbarrier
+  int stag_window;              // >0: stop when |r| has not halved over this many iterations
+  double *coefA;                // dense: per-row coefficients of the column pass (m)
+  // register-streamed CSR (FP32 products)
+  const RowSlot *rslot;
+  const float4 *rval4;
+  const int4 *rcol4;
+  int rws;                      // per-warp accumulator stride (floats, multiple of 32)
+  int pf_dist;                  // L2 prefetch distance in warp steps (0: off)
 };
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
@@ -198,38 +206,94 @@ struct OpCsr {
 };
 
 // ---------------------------------------------------------------- DENSE (explicit H, dense A, C)
+// Eight consecutive entries of a row as T (16-byte loads; the caller checks
+// that the address is aligned to 8 entries).
+template <class S, class T> struct Load8;
+template <class T> struct Load8<__nv_bfloat16, T> {
+  static __device__ __forceinline__ void run(const __nv_bfloat16 *p, T (&v)[8]) {
+    const uint4 u = __ldg(reinterpret_cast<const uint4 *>(p));
+    const __nv_bfloat162 *b = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const float2 f = __bfloat1622float2(b[k]);
+      v[2 * k] = (T)f.x;
+      v[2 * k + 1] = (T)f.y;
+    }
+  }
+};
+template <class T> struct Load8<float, T> {
+  static __device__ __forceinline__ void run(const float *p, T (&v)[8]) {
+    const float4 x = __ldg(reinterpret_cast<const float4 *>(p));
+    const float4 y = __ldg(reinterpret_cast<const float4 *>(p) + 1);
+    v[0] = (T)x.x; v[1] = (T)x.y; v[2] = (T)x.z; v[3] = (T)x.w;
+    v[4] = (T)y.x; v[5] = (T)y.y; v[6] = (T)y.z; v[7] = (T)y.w;
+  }
+};
+template <class T> struct Load8<double, T> {
+  static __device__ __forceinline__ void run(const double *p, T (&v)[8]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const double2 x = __ldg(reinterpret_cast<const double2 *>(p) + k);
+      v[2 * k] = (T)x.x;
+      v[2 * k + 1] = (T)x.y;
+    }
+  }
+};
+
+// dot of one row with the p window; vectorised when the rows are 8-aligned
+template <class S, class T>
+__device__ __forceinline__ T row_dot(const S *r, const T *pw, int64_t n, bool vec, int lane) {
+  T dot = (T)0;
+  if (vec) {
+    for (int64_t j = 8 * lane; j < n; j += 256) {
+      T v[8];
+      Load8<S, T>::run(r + j, v);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) dot += v[k] * pw[j + k];   // pw is zero beyond n
+    }
+  } else {
+    for (int64_t j = lane; j < n; j += 32) dot += (T)ld_as_f64(r, j) * pw[j];
+  }
+  return warp_sum(dot);
+}
+
 template <class HS, class AS>
 struct OpDense {
   // vcta / vG: this CTA's rank and the number of CTAs working on the problem
-  // (the whole grid for a single problem, a team in the batched solver)
+  // (the whole grid for a single problem, a team in the batched solver).
+  // For n >= 512 the A' part is a second, column-blocked pass over A after a
+  // barrier (register accumulation, no shared-memory atomics); small problems
+  // scatter each row's coefficient with shared atomics in the same pass.
   template <class T>
   static __device__ double phaseA(const PcgArgs &a, const double *ysrc, const double *pold,
                                   double *pnew, double beta, int64_t vb, int64_t ve,
-                                  unsigned char *smem, int vcta, int vG) {
+                                  unsigned char *smem, int vcta, int vG, bool &ok) {
     const DevProb &P = a.P;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = blockDim.x >> 5;
     const int64_t n = P.n, m = P.m, me = P.me;
+    const int64_t hld = P.hld > 0 ? P.hld : n, ald = P.ald > 0 ? P.ald : n;
+    const int64_t npad = (n + 7) & ~(int64_t)7;
     T *pw = reinterpret_cast<T *>(smem);
     T *acc = pw + a.win_cap;
     T *accg = reinterpret_cast<T *>(a.accx);
+    const HS *Hd = reinterpret_cast<const HS *>(P.Hd);
+    const AS *Ad = reinterpret_cast<const AS *>(P.Ad);
+    const bool hvec = (hld % 8 == 0) && ((reinterpret_cast<uintptr_t>(Hd) & 15) == 0);
+    const bool avec = (ald % 8 == 0) && ((reinterpret_cast<uintptr_t>(Ad) & 15) == 0);
+    const bool colpass = n >= 512 && m > 0 && a.coefA != nullptr && avec;
     double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
-    for (int64_t j = tid; j < n; j += blockDim.x) {
-      pw[j] = (T)(ldcg(ysrc + j) + beta * ldcg(pold + j));
+    for (int64_t j = tid; j < npad; j += blockDim.x) {
+      pw[j] = j < n ? (T)(ldcg(ysrc + j) + beta * ldcg(pold + j)) : (T)0;
       acc[j] = (T)0;
     }
     __syncthreads();
-    const HS *Hd = reinterpret_cast<const HS *>(P.Hd);
-    const AS *Ad = reinterpret_cast<const AS *>(P.Ad);
     const int64_t R = n + m + me;
     const int64_t gw0 = (int64_t)vcta * nw + warp, GW = (int64_t)vG * nw;
     const int64_t lo_off = n + me, up_off = n + me + m;
     for (int64_t row = gw0; row < R; row += GW) {
       if (row < n) {
-        const HS *h = Hd + row * n;
-        T dot = (T)0;
-        for (int64_t j = lane; j < n; j += 32) dot += (T)ld_as_f64(h, j) * pw[j];
-        dot = warp_sum(dot) * (T)P.hscale;
+        const T dot = row_dot<HS, T>(Hd + row * hld, pw, n, hvec, lane) * (T)P.hscale;
         if (lane == 0) {
           atomicAdd(acc + row, dot);
           const double prow = ldcg(ysrc + row) + beta * ldcg(pold + row);
@@ -239,20 +303,26 @@ struct OpDense {
         const int64_t ai = row - n;
         const bool hl = P.hasl[ai] != 0, hu = P.hasu[ai] != 0;
         if (!hl && !hu) {
-          if (lane == 0) { a.qlam[me + ai] = 0.0; a.qlam[me + m + ai] = 0.0; }
+          if (lane == 0) {
+            a.qlam[me + ai] = 0.0;
+            a.qlam[me + m + ai] = 0.0;
+            if (colpass) a.coefA[ai] = 0.0;
+          }
           continue;
         }
-        const AS *ar = Ad + ai * n;
-        T dot = (T)0;
-        for (int64_t j = lane; j < n; j += 32) dot += (T)ld_as_f64(ar, j) * pw[j];
-        dot = warp_sum(dot);
+        const AS *ar = Ad + ai * ald;
+        const T dot = row_dot<AS, T>(ar, pw, n, avec, lane);
         const double rho_a = P.rhoA[ai];
         const double t = rho_a * (double)dot;
         const double pl = hl ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
         const double pu = hu ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
         const double coef = 2.0 * t * (a.cl[ai] + a.cu[ai]) + pl - pu;
-        const T cf = (T)(coef * rho_a);
-        for (int64_t j = lane; j < n; j += 32) atomicAdd(acc + j, cf * (T)ld_as_f64(ar, j));
+        if (colpass) {
+          if (lane == 0) a.coefA[ai] = coef * rho_a;
+        } else {
+          const T cf = (T)(coef * rho_a);
+          for (int64_t j = lane; j < n; j += 32) atomicAdd(acc + j, cf * (T)ld_as_f64(ar, j));
+        }
         if (lane == 0) {
           const double ql = hl ? t + a.Dl[ai] * pl : 0.0;
           const double qu = hu ? -t + a.Du[ai] * pu : 0.0;
@@ -282,6 +352,36 @@ struct OpDense {
     for (int64_t j = tid; j < n; j += blockDim.x) {
       const T v = acc[j];
       if (v != (T)0) atomicAdd(accg + j, v);
+    }
+    if (colpass) {
+      // A' (rho coef): tasks = (256-column block) x (slice of rows)
+      ok = grid_sync(a.bar);
+      if (!ok) return 0.0;
+      const int64_t nblk = (n + 255) / 256;
+      int64_t nrs = (4 * GW + nblk - 1) / nblk;
+      nrs = nrs < 1 ? 1 : (nrs > m ? m : nrs);
+      const int64_t rows_per = (m + nrs - 1) / nrs;
+      for (int64_t task = gw0; task < nblk * nrs; task += GW) {
+        const int64_t blk = task % nblk, rs = task / nblk;
+        const int64_t c0 = blk * 256 + 8 * lane;
+        const int64_t a0 = rs * rows_per, a1 = (a0 + rows_per < m) ? a0 + rows_per : m;
+        T s8[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) s8[k] = (T)0;
+        if (c0 < n) {
+          for (int64_t ai = a0; ai < a1; ++ai) {
+            const T cf = (T)__ldcg(a.coefA + ai);
+            if (cf == (T)0) continue;
+            T v[8];
+            Load8<AS, T>::run(Ad + ai * ald + c0, v);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) s8[k] += cf * v[k];
+          }
+#pragma unroll
+          for (int k = 0; k < 8; ++k)
+            if (c0 + k < n && s8[k] != (T)0) atomicAdd(accg + c0 + k, s8[k]);
+        }
+      }
     }
     return pq;
   }
@@ -789,8 +889,220 @@ struct OpCsrStaged {
   }
 };
 
+// ---------------------------------------------------------------- CSR, register-streamed
+// Shared memory of the register-streamed operator: the p window, one private
+// accumulator per warp (no atomics in the scatter), the dose-limit constants.
+struct RowsLayout { size_t pw, acc, arho, acs, aDl, aDu, apl, apu, afl, total; };
+__host__ __device__ inline RowsLayout rows_layout(int rws, int nw, int a_cap) {
+  RowsLayout L;
+  size_t o = 0;
+  L.pw = o; o += 4 * (size_t)rws;
+  L.acc = o; o += 4 * (size_t)rws * nw;
+  L.arho = o; o += 4 * (size_t)a_cap;
+  L.acs = o; o += 4 * (size_t)a_cap;
+  L.aDl = o; o += 4 * (size_t)a_cap;
+  L.aDu = o; o += 4 * (size_t)a_cap;
+  L.apl = o; o += 4 * (size_t)a_cap;
+  L.apu = o; o += 4 * (size_t)a_cap;
+  L.afl = o; o += (size_t)a_cap;
+  L.total = kq_up128(o);
+  return L;
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  if (bytes >= 16)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes & ~15u) : "memory");
+}
+
+// Every warp walks its own rows (pairs 2w, 2w+1, then +2 NW, ...) with plain
+// 16-byte loads straight into registers, the next pair's loads in flight
+// while the current pair is processed; thread 0 prefetches the CTA's rows a
+// few warp steps ahead into L2.  No shared-memory staging and no CTA barrier
+// inside the product.  The scatter goes into the warp's private accumulator
+// with plain read-modify-write: the columns of one row are distinct (padding
+// included), and __syncwarp orders the rows of a warp.  The private copies
+// are summed once per product.
+struct OpCsrRows {
+  struct Pair { RowSlot s0, s1; float4 v0, v1; int4 c0, c1; };
+
+  static __device__ __forceinline__ void load_pair(const PcgArgs &a, const RowSlot *S, int i,
+                                                   int nr, int lane, Pair &q) {
+    const float4 fz = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int4 iz = make_int4(0, 0, 0, 0);
+    q.s0 = RowSlot{0, 0, -1, 0.f};
+    q.s1 = RowSlot{0, 0, -1, 0.f};
+    q.v0 = fz; q.v1 = fz; q.c0 = iz; q.c1 = iz;
+    if (i < nr) {
+      q.s0 = S[i];
+      if (lane < q.s0.len4) {
+        q.v0 = __ldcs(a.rval4 + q.s0.off4 + lane);
+        q.c0 = __ldcs(a.rcol4 + q.s0.off4 + lane);
+      }
+    }
+    if (i + 1 < nr) {
+      q.s1 = S[i + 1];
+      if (lane < q.s1.len4) {
+        q.v1 = __ldcs(a.rval4 + q.s1.off4 + lane);
+        q.c1 = __ldcs(a.rcol4 + q.s1.off4 + lane);
+      }
+    }
+  }
+
+  // thread 0: L2 prefetch of warp step `step` (rows [step*2nw, (step+1)*2nw))
+  static __device__ __forceinline__ void prefetch_step(const PcgArgs &a, const RowSlot *S, int step,
+                                                       int nr, int nw) {
+    const int r0 = step * 2 * nw;
+    if (r0 >= nr) return;
+    const int r1 = min(nr, r0 + 2 * nw) - 1;
+    const RowSlot f = S[r0], l = S[r1];
+    const uint32_t bytes = (uint32_t)(l.off4 + l.len4 - f.off4) * 16u;
+    prefetch_l2(a.rval4 + f.off4, bytes);
+    prefetch_l2(a.rcol4 + f.off4, bytes);
+  }
+
+  template <class T>
+  static __device__ void begin(const PcgArgs &a, unsigned char *smem) {
+    const int cta = blockIdx.x, tid = threadIdx.x, nw = blockDim.x >> 5;
+    const RowsLayout L = rows_layout(a.rws, nw, a.a_cap);
+    float *acc = reinterpret_cast<float *>(smem + L.acc);
+    for (int j = tid; j < a.rws * nw; j += blockDim.x) acc[j] = 0.f;
+    const int alo = a.a_lo[cta], na = min(a.a_hi[cta] - alo, a.a_cap);
+    float *arho = reinterpret_cast<float *>(smem + L.arho);
+    float *acs = reinterpret_cast<float *>(smem + L.acs);
+    float *aDl = reinterpret_cast<float *>(smem + L.aDl);
+    float *aDu = reinterpret_cast<float *>(smem + L.aDu);
+    uint8_t *afl = smem + L.afl;
+    for (int i = tid; i < na; i += blockDim.x) {
+      const int ai = alo + i;
+      arho[i] = (float)a.P.rhoA[ai];
+      acs[i] = (float)(a.cl[ai] + a.cu[ai]);
+      aDl[i] = (float)a.Dl[ai];
+      aDu[i] = (float)a.Du[ai];
+      afl[i] = (uint8_t)((a.P.hasl[ai] ? 1 : 0) | (a.P.hasu[ai] ? 2 : 0));
+    }
+    if (tid == 0 && a.pf_dist > 0) {
+      const int64_t r0 = a.row_begin[cta];
+      const int nr = (int)(a.row_begin[cta + 1] - r0);
+      for (int s = 0; s < a.pf_dist; ++s) prefetch_step(a, a.rslot + r0, s, nr, nw);
+    }
+    __syncthreads();
+  }
+
+  // one row's scatter into the warp's accumulator (columns distinct)
+  static __device__ __forceinline__ void scatter(float *accw, const float4 &v, const int4 &c,
+                                                 float u, bool act) {
+    if (act) {
+      const float a0 = accw[c.x], a1 = accw[c.y], a2 = accw[c.z], a3 = accw[c.w];
+      accw[c.x] = fmaf(u, v.x, a0);
+      accw[c.y] = fmaf(u, v.y, a1);
+      accw[c.z] = fmaf(u, v.z, a2);
+      accw[c.w] = fmaf(u, v.w, a3);
+    }
+    __syncwarp();
+  }
+
+  template <class T>
+  static __device__ double phaseA(const PcgArgs &a, const double *ysrc, const double *pold,
+                                  double *pnew, double beta, int64_t vb, int64_t ve,
+                                  unsigned char *smem, bool &ok) {
+    static_assert(sizeof(T) == 4, "register-streamed CSR runs FP32 products");
+    const DevProb &P = a.P;
+    const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nw = blockDim.x >> 5;
+    const RowsLayout L = rows_layout(a.rws, nw, a.a_cap);
+    const int lo = a.win_lo[cta], wlen = a.win_hi[cta] - lo;
+    float *pw = reinterpret_cast<float *>(smem + L.pw);
+    float *acc = reinterpret_cast<float *>(smem + L.acc);
+    float *accw = acc + (size_t)warp * a.rws;
+    float *accg = reinterpret_cast<float *>(a.accx);
+    const int alo = a.a_lo[cta], na = min(a.a_hi[cta] - alo, a.a_cap);
+    const float *arho = reinterpret_cast<const float *>(smem + L.arho);
+    const float *acs = reinterpret_cast<const float *>(smem + L.acs);
+    const float *aDl = reinterpret_cast<const float *>(smem + L.aDl);
+    const float *aDu = reinterpret_cast<const float *>(smem + L.aDu);
+    float *apl = reinterpret_cast<float *>(smem + L.apl);
+    float *apu = reinterpret_cast<float *>(smem + L.apu);
+    const uint8_t *afl = smem + L.afl;
+    const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
+    const int64_t r0 = a.row_begin[cta];
+    const int nr = (int)(a.row_begin[cta + 1] - r0);
+    const RowSlot *S = a.rslot + r0;
+    // the first pair's loads do not depend on p: start them before the window
+    Pair cur;
+    int i = 2 * warp;
+    load_pair(a, S, i, nr, lane, cur);
+    double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
+    for (int j = tid; j < wlen; j += blockDim.x) {
+      const int c = lo + j;
+      pw[j] = (float)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+    }
+    for (int k = tid; k < na; k += blockDim.x) {
+      const int ai = alo + k;
+      apl[k] = (float)((afl[k] & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0);
+      apu[k] = (float)((afl[k] & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0);
+    }
+    __syncthreads();
+    float pqt = 0.f;
+    int step = 0;
+    for (; i < nr; i += 2 * nw, ++step) {
+      if (tid == 0 && a.pf_dist > 0) prefetch_step(a, S, step + a.pf_dist, nr, nw);
+      Pair nxt;
+      load_pair(a, S, i + 2 * nw, nr, lane, nxt);
+      const bool act0 = lane < cur.s0.len4, act1 = lane < cur.s1.len4;
+      float d0 = 0.f, d1 = 0.f;
+      if (act0)
+        d0 = cur.v0.x * pw[cur.c0.x] + cur.v0.y * pw[cur.c0.y] + cur.v0.z * pw[cur.c0.z] +
+             cur.v0.w * pw[cur.c0.w];
+      if (act1)
+        d1 = cur.v1.x * pw[cur.c1.x] + cur.v1.y * pw[cur.c1.y] + cur.v1.z * pw[cur.c1.z] +
+             cur.v1.w * pw[cur.c1.w];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+        d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+      }
+      const RowDesc rd0{0, cur.s0.a, cur.s0.w2, 0.f}, rd1{0, cur.s1.a, cur.s1.w2, 0.f};
+      const float u0 = OpCsrStaged::row_coef<float>(a, rd0, d0, ysrc, pold, beta, alo, na, arho, acs,
+                                                    aDl, aDu, apl, apu, afl, lane, pqt);
+      float u1 = 0.f;
+      if (i + 1 < nr)
+        u1 = OpCsrStaged::row_coef<float>(a, rd1, d1, ysrc, pold, beta, alo, na, arho, acs, aDl,
+                                          aDu, apl, apu, afl, lane, pqt);
+      if (lane == 0) pqt += u0 * d0 + u1 * d1;
+      scatter(accw, cur.v0, cur.c0, u0, act0);
+      scatter(accw, cur.v1, cur.c1, u1, act1);
+      cur = nxt;
+    }
+    __syncthreads();
+    // sum the private copies into the global accumulator; zero them
+    float4 *acc4 = reinterpret_cast<float4 *>(acc);
+    const int ws4 = a.rws >> 2;
+    for (int j4 = tid; j4 < ws4; j4 += blockDim.x) {
+      float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int w = 0; w < nw; ++w) {
+        const float4 x = acc4[(size_t)w * ws4 + j4];
+        t.x += x.x; t.y += x.y; t.z += x.z; t.w += x.w;
+        acc4[(size_t)w * ws4 + j4] = make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+      const int c = 4 * j4;
+      if (c + 0 < wlen && t.x != 0.f) atomicAdd(accg + lo + c + 0, t.x);
+      if (c + 1 < wlen && t.y != 0.f) atomicAdd(accg + lo + c + 1, t.y);
+      if (c + 2 < wlen && t.z != 0.f) atomicAdd(accg + lo + c + 2, t.z);
+      if (c + 3 < wlen && t.w != 0.f) atomicAdd(accg + lo + c + 3, t.w);
+    }
+    // prefetch the first steps of the next product (the matrix does not change)
+    if (tid == 0 && a.pf_dist > 0)
+      for (int s2 = 0; s2 < a.pf_dist; ++s2) prefetch_step(a, S, s2, nr, nw);
+    (void)ok;
+    return pq + (double)pqt;
+  }
+};
+
 template <class OP> struct IsStaged { static constexpr bool value = false; };
 template <> struct IsStaged<OpCsrStaged> { static constexpr bool value = true; };
+
+template <class OP> struct IsRows { static constexpr bool value = false; };
+template <> struct IsRows<OpCsrRows> { static constexpr bool value = true; };
 
 template <class OP> struct IsLowrank { static constexpr bool value = false; };
 template <class ZS> struct IsLowrank<OpLowrank<ZS>> { static constexpr bool value = true; };
@@ -800,14 +1112,15 @@ __device__ __forceinline__ double run_phaseA(const PcgArgs &a, const double *ysr
                                              const double *pold, double *pnew, double beta,
                                              int64_t vb, int64_t ve, unsigned char *smem,
                                              PipeState &ps, bool &ok, int vcta, int vG) {
-  if constexpr (IsLowrank<OP>::value) {
+  if constexpr (IsLowrank<OP>::value || IsRows<OP>::value) {
+    ok = true;
     return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ok);
   } else if constexpr (IsStaged<OP>::value) {
     ok = true;
     return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ps, ok);
   } else {
     ok = true;
-    return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, vcta, vG);
+    return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, vcta, vG, ok);
   }
 }
 
@@ -828,6 +1141,7 @@ __device__ void pcg_body(const PcgArgs &a, const int cta, const int G, unsigned 
   const double *ysrc = a.apply ? a.rhs : a.y;
   PipeState ps;
   if constexpr (IsStaged<OP>::value) OP::template begin<T>(a, smem, ps);
+  if constexpr (IsRows<OP>::value) OP::template begin<T>(a, smem);
 
   // ---- initialisation: z = 0, r = rhs, y = r / diag, p_old = 0
   {
@@ -856,8 +1170,14 @@ __device__ void pcg_body(const PcgArgs &a, const int cta, const int G, unsigned 
     rho = sum_slots(a.slots + G, G, sh);
     rr = bb;
   }
+  double rr_mark = bb;
   while (ok) {
     if (!a.apply && (rr <= a.tol2 * bb || it >= a.maxit)) break;
+    // FP32 correction passes: hand over to the FP64 pass once they stagnate
+    if (a.stag_window > 0 && it > 0 && it % a.stag_window == 0) {
+      if (rr > 0.25 * rr_mark) break;
+      rr_mark = rr;
+    }
     // ---- phase A: q = K p,  p = y + beta p_old
     double pq = run_phaseA<OP, T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ps, ok, cta, G);
     if (!ok) break;
@@ -1039,7 +1359,7 @@ template <class X> X *dalloc(kq_problem *h, size_t count) {
 kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double tol, int maxit,
                  int apply, int *iters_out, double *rr_out, double *bb_out) {
   PcgWork &W = h->W;
-  PcgArgs a;
+  PcgArgs a{};
   a.P = h->P;
   a.Dl = h->K.Dl; a.Du = h->K.Du; a.cl = h->K.cl; a.cu = h->K.cu;
   a.dg = h->K.dg; a.diag = h->K.diag; a.mu = h->K.mu;
@@ -1059,15 +1379,27 @@ kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double t
   a.copy_piece = W.copy_piece;
   a.stages = W.stages;
   a.producer = W.producer;
+  a.stag_window = (prec == KQ_PREC_MIXED && !apply) ? 200 : 0;
+  a.coefA = W.coefA;
+  a.rslot = W.rslot;
+  a.rval4 = reinterpret_cast<const float4 *>(W.rval);
+  a.rcol4 = reinterpret_cast<const int4 *>(W.rcol);
+  a.rws = W.rws;
+  a.pf_dist = W.pf_dist;
   KFun f = prec == KQ_PREC_MIXED ? pick_kernel<float>(h->P) : pick_kernel<double>(h->P);
+  size_t smem = W.smem;
+  if (prec == KQ_PREC_MIXED && W.rows_ok) {
+    f = pcg_kernel<OpCsrRows, float>;
+    smem = W.smem_rows;
+  }
   KQ_CUDA(h, cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)W.smem));
+                                  (int)smem));
   KQ_CUDA(h, cudaMemsetAsync(W.err, 0, sizeof(int), h->stream));
   KQ_CUDA(h, cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), h->stream));
   void *args[] = {&a};
   KQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
   KQ_CUDA(h, cudaLaunchCooperativeKernel((const void *)f, dim3(W.G), dim3(W.threads), args,
-                                         W.smem, h->stream));
+                                         smem, h->stream));
   ++h->launches;
   ++h->pcg_launches;
   KQ_CUDA(h, cudaEventRecord(h->ev1, h->stream));
@@ -1117,14 +1449,15 @@ kq_status pcg_dense_raw(const DevProb &P, const double *Dl, const double *Du, co
   a.rhs = rhs; a.z = z;
   a.r = w.r; a.y = w.y; a.pb0 = w.pb0; a.pb1 = w.pb1; a.qlam = w.qlam;
   a.accx = w.accx; a.g = nullptr; a.slots = w.slots;
-  a.row_begin = nullptr; a.win_lo = nullptr; a.win_hi = nullptr; a.win_cap = (int)P.n;
+  a.row_begin = nullptr; a.win_lo = nullptr; a.win_hi = nullptr;
+  a.win_cap = (int)((P.n + 7) & ~(int64_t)7);
   a.bar.count = w.bar; a.bar.gen = w.bar + 1; a.bar.err = w.err; a.bar.nblocks = (unsigned)G;
   a.bar.budget_ns = (uint64_t)(timeout_s * 1e9);
   a.tol2 = tol * tol; a.maxit = maxit; a.apply = 0;
   a.iters = w.iters; a.resn = w.resn;
   a.stages = 2; a.producer = 0; a.copy_piece = 16;
   KFun f = pcg_kernel<OpDense<double, double>, double>;
-  const size_t smem = (size_t)2 * P.n * sizeof(double);
+  const size_t smem = (size_t)2 * a.win_cap * sizeof(double);
   const int threads = 512;
   auto fail = [&](const char *what, cudaError_t e) {
     if (msg) *msg = std::string(what) + ": " + cudaGetErrorString(e);
@@ -1281,14 +1614,16 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
     a.r = W.r; a.y = W.y; a.pb0 = W.pb0; a.pb1 = W.pb1; a.qlam = W.qlam;
     a.accx = prec == KQ_PREC_MIXED ? (void *)W.accx32 : (void *)W.accx64;
     a.g = nullptr; a.slots = W.slots;
-    a.win_cap = (int)h->n;
+    a.win_cap = (int)((h->n + 7) & ~(int64_t)7);
     a.bar.count = W.bar; a.bar.gen = W.bar + 1; a.bar.err = B.d_err + j;
     a.bar.nblocks = (unsigned)teams[team_of[j]].size;
     a.bar.budget_ns = (uint64_t)(h->timeout_s * 1e9);
     a.tol2 = tol[j] * tol[j]; a.maxit = maxit[j]; a.apply = apply;
     a.iters = B.d_iters + j; a.resn = B.d_resn + 2 * j;
     a.stages = 2; a.producer = 0; a.copy_piece = 16;
-    smem = std::max(smem, (size_t)2 * h->n * (prec == KQ_PREC_MIXED ? sizeof(float) : sizeof(double)));
+    a.stag_window = (prec == KQ_PREC_MIXED && !apply) ? 200 : 0;
+    a.coefA = W.coefA;
+    smem = std::max(smem, (size_t)2 * a.win_cap * (prec == KQ_PREC_MIXED ? sizeof(float) : sizeof(double)));
     if (cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) { err = "memset"; return KQ_ERR_CUDA; }
   }
   const kq_problem *h0 = hs[idx[0]];
@@ -1358,6 +1693,148 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
 
 double pcg_last_kernel_ms() { return g_last_ms; }
 
+// Fill of the register-streamed layout, one warp per row of P.  The row's
+// nonzeros are ranked by (multiplicity of their bank in the row, descending;
+// bank; position) and rank i goes to lane i/4, component i%4, so entries of
+// one bank are dealt to different load components.  Padding slots get value
+// 0 and a window column outside the row, preferably on a bank that their
+// component does not use yet.  err[0] = 1 if a row has no room for padding.
+__global__ void k_rows_fill(const int64_t *rowptr, const int32_t *col, const float *val,
+                            const RowSlot *slots, const int64_t *row_begin,
+                            const int32_t *win_lo, const int32_t *win_hi, int G, int64_t nP,
+                            float *rv, int32_t *rc, int *err) {
+  __shared__ int s_key[8][128];
+  __shared__ int s_rel[8][128];
+  __shared__ int s_cnt[8][32];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t r = gw; r < nP; r += nwarps) {
+    int lo_c = 0, hi_c = G;            // CTA of row r: row_begin[c] <= r < row_begin[c+1]
+    while (hi_c - lo_c > 1) {
+      const int mid = (lo_c + hi_c) >> 1;
+      if (row_begin[mid] <= r) lo_c = mid; else hi_c = mid;
+    }
+    const int lo = win_lo[lo_c], wl = win_hi[lo_c] - lo;
+    const int64_t s0 = rowptr[r];
+    const int len = (int)(rowptr[r + 1] - s0);
+    const RowSlot sl = slots[r];
+    const int64_t base = 4 * (int64_t)sl.off4;
+    s_cnt[wib][lane] = 0;
+    __syncwarp();
+    for (int e = lane; e < len; e += 32) {
+      const int rel = col[s0 + e] - lo;
+      s_rel[wib][e] = rel;
+      atomicAdd(&s_cnt[wib][rel & 31], 1);
+    }
+    __syncwarp();
+    for (int e = lane; e < len; e += 32) {
+      const int b = s_rel[wib][e] & 31;
+      s_key[wib][e] = ((32 - s_cnt[wib][b]) << 12) | (b << 7) | e;
+    }
+    __syncwarp();
+    uint32_t used[4] = {0u, 0u, 0u, 0u};
+    for (int e = lane; e < len; e += 32) {
+      const int key = s_key[wib][e];
+      int rank = 0;
+      for (int j = 0; j < len; ++j) rank += s_key[wib][j] < key;
+      const int q = rank & 3, ln = rank >> 2;
+      rv[base + 4 * ln + q] = val[s0 + e];
+      rc[base + 4 * ln + q] = s_rel[wib][e];
+      used[q] |= 1u << (s_rel[wib][e] & 31);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) used[q] = __reduce_or_sync(0xffffffffu, used[q]);
+    int nrow = len;                     // s_rel[0..nrow) = columns taken in this row
+    for (int i = len; i < 4 * sl.len4; ++i) {
+      const int q = i & 3, ln = i >> 2;
+      int pick = -1;
+      for (int pass = 0; pass < 2 && pick < 0; ++pass) {
+        for (int c0 = 0; c0 < wl && pick < 0; c0 += 32) {
+          const int c = c0 + lane;
+          bool okc = c < wl && (pass == 1 || !((used[q] >> (c & 31)) & 1u));
+          if (okc)
+            for (int j = 0; j < nrow; ++j)
+              if (s_rel[wib][j] == c) { okc = false; break; }
+          const unsigned bal = __ballot_sync(0xffffffffu, okc);
+          if (bal) pick = c0 + __ffs(bal) - 1;
+        }
+      }
+      if (pick < 0) {
+        if (lane == 0) atomicExch(err, 1);
+        break;
+      }
+      if (lane == 0) {
+        rv[base + 4 * ln + q] = 0.f;
+        rc[base + 4 * ln + q] = pick;
+        s_rel[wib][nrow] = pick;
+      }
+      used[q] |= 1u << (pick & 31);
+      ++nrow;
+      __syncwarp();
+    }
+    __syncwarp();
+  }
+}
+
+// Register-streamed CSR layout (FP32 products).  Eligible when every row has
+// at most 128 nonzeros, every CTA's window leaves room for the padding
+// columns, and the per-warp accumulators fit in shared memory.  Returns
+// false (and leaves the staged operator in charge) otherwise.
+bool build_rows_layout(kq_problem *h, int G, int threads, const std::vector<int64_t> &rb,
+                       const std::vector<int64_t> &rp, const std::vector<int32_t> &lo,
+                       const std::vector<int32_t> &hi, const std::vector<int32_t> &p2a,
+                       const std::vector<double> &w2) {
+  PcgWork &W = h->W;
+  const DevProb &P = h->P;
+  if (getenv("KQ_STAGED")) return false;
+  const int64_t nP = P.nP;
+  int wmax = 1;
+  for (int c = 0; c < G; ++c) wmax = std::max(wmax, hi[c] - lo[c]);
+  const int rws = (wmax + 31) & ~31;
+  const int nw = threads / 32;
+  const size_t smem = rows_layout(rws, nw, W.a_cap).total;
+  if (smem > 220 * 1024) return false;
+  std::vector<RowSlot> slots(std::max<int64_t>(nP, 1));
+  int64_t tot4 = 0;
+  for (int c = 0; c < G; ++c) {
+    const int wl = hi[c] - lo[c];
+    for (int64_t r = rb[c]; r < rb[c + 1]; ++r) {
+      const int64_t len = rp[r + 1] - rp[r], len4 = (len + 3) / 4;
+      if (len > 128 || 4 * len4 > wl) return false;
+      slots[r] = RowSlot{(int32_t)tot4, (int32_t)len4, p2a[r], (float)w2[r]};
+      tot4 += len4;
+      if (tot4 > INT32_MAX / 2) return false;
+    }
+  }
+  W.rslot = dalloc<RowSlot>(h, slots.size());
+  W.rval = dalloc<float>(h, 4 * (tot4 + 1));
+  W.rcol = dalloc<int32_t>(h, 4 * (tot4 + 1));
+  int *d_err = dalloc<int>(h, 1);
+  if (!W.rslot || !W.rval || !W.rcol || !d_err) return false;
+  if (cudaMemcpy(W.rslot, slots.data(), slots.size() * sizeof(RowSlot), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemsetAsync(d_err, 0, sizeof(int), h->stream) != cudaSuccess)
+    return false;
+  if (nP > 0) {
+    const int blocks = (int)std::min<int64_t>(ceil_div64(nP, 8), 4096);
+    k_rows_fill<<<blocks, 256, 0, h->stream>>>(P.rowptr, P.col, P.val, W.rslot, W.row_begin,
+                                                W.win_lo, W.win_hi, G, nP, W.rval, W.rcol, d_err);
+    ++h->launches;
+  }
+  int e = 0;
+  if (cudaGetLastError() != cudaSuccess ||
+      cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+      cudaStreamSynchronize(h->stream) != cudaSuccess || e != 0)
+    return false;
+  W.rws = rws;
+  W.smem_rows = smem;
+  {
+    const char *pf = getenv("KQ_PF");
+    W.pf_dist = pf ? std::max(0, atoi(pf)) : 2;
+  }
+  return true;
+}
+
 kq_status pcg_setup(kq_problem *h, int grid_ctas) {
   PcgWork &W = h->W;
   const DevProb &P = h->P;
@@ -1367,8 +1844,8 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
   int win_cap = 0;
   if (P.hkind == KQ_H_DENSE) {
     threads = 512;
-    win_cap = (int)n;
-    smem = (size_t)2 * n * sizeof(double);
+    win_cap = (int)((n + 7) & ~(int64_t)7);
+    smem = (size_t)2 * win_cap * sizeof(double);
     if (smem > 200 * 1024)
       return kq_fail(h, KQ_ERR_ARG, "dense H: n too large for the single-problem kernel");
   }
@@ -1520,6 +1997,8 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
     KQ_CUDA(h, cudaMemcpy(W.cta_chunk, cta_chunk.data(), (G + 1) * sizeof(int32_t), cudaMemcpyHostToDevice));
     KQ_CUDA(h, cudaMemcpy(W.a_lo, alo.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice));
     KQ_CUDA(h, cudaMemcpy(W.a_hi, ahi.data(), G * sizeof(int32_t), cudaMemcpyHostToDevice));
+    W.rows_ok = build_rows_layout(h, G, threads, rb, rp, lo, hi, p2a, w2);
+    cudaGetLastError();
   } else if (P.hkind == KQ_H_LOWRANK) {
     int64_t rmax = 0;
     for (int c = 0; c < G; ++c) rmax = std::max(rmax, rb[c + 1] - rb[c]);
@@ -1545,6 +2024,12 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
     KQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f32, threads, smem));
     if (per_sm * sms < G)
       return kq_fail(h, KQ_ERR_ARG, "persistent PCG grid (mixed) does not fit on the device");
+    if (W.rows_ok) {
+      const void *fr = (const void *)pcg_kernel<OpCsrRows, float>;
+      KQ_CUDA(h, cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W.smem_rows));
+      KQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fr, threads, W.smem_rows));
+      if (per_sm * sms < G) W.rows_ok = false;
+    }
   }
   W.r = dalloc<double>(h, nkp);
   W.y = dalloc<double>(h, nkp);
@@ -1554,13 +2039,14 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
   W.accx64 = dalloc<double>(h, n);
   W.accx32 = dalloc<float>(h, n);
   W.g64 = dalloc<double>(h, P.k + P.me + 1);
+  W.coefA = dalloc<double>(h, P.m + 1);
   W.slots = dalloc<double>(h, 4 * G);
   W.bar = dalloc<unsigned int>(h, 2);
   W.err = dalloc<int>(h, 1);
   W.iters = dalloc<int>(h, 1);
   W.resn = dalloc<double>(h, 2);
   if (!W.r || !W.y || !W.pb0 || !W.pb1 || !W.qlam || !W.accx64 || !W.accx32 || !W.g64 ||
-      !W.slots || !W.bar || !W.err || !W.iters || !W.resn)
+      !W.slots || !W.bar || !W.err || !W.iters || !W.resn || !W.coefA)
     return kq_fail(h, KQ_ERR_OOM, "pcg work space");
   KQ_CUDA(h, cudaMemset(W.accx64, 0, n * sizeof(double)));
   KQ_CUDA(h, cudaMemset(W.accx32, 0, n * sizeof(float)));
@@ -1607,6 +2093,7 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
     rc = launch(h, prec, res, dz, rel, budget, 0, &it, nullptr, nullptr);
     s.kernel_ms += g_last_ms;
     total += it;
+    if (prec == KQ_PREC_F64) s.iters_f64 += it;
     s.passes++;
     if (rc != KQ_OK) break;
     k_add<<<256, 256, 0, h->stream>>>(N, z, dz);

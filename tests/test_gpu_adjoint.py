@@ -86,7 +86,9 @@ def test_qp_layer_autograd(kq):
     h = kq.create_from(qp)
     xs = np.zeros(qp.n)
     kq.ipm_solve(h, x=xs)
-    assert np.max(np.abs(x.detach().cpu().numpy() - xs)) <= 1e-12 * (1 + np.max(np.abs(xs)))
+    # same solve twice: the K*v scatter sums with atomics, so the rounding
+    # order (not the method) may differ between the two runs
+    assert np.max(np.abs(x.detach().cpu().numpy() - xs)) <= 1e-9 * (1 + np.max(np.abs(xs)))
     gp, glA, guA, gb = _gpu_backward(kq, h, gbar.cpu().numpy(), tol=1e-7)
     assert _rel(p.grad.cpu().numpy(), gp) <= 1e-5
     assert _rel(lA.grad.cpu().numpy(), glA) <= 1e-5

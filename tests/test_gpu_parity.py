@@ -105,6 +105,24 @@ def test_kkt_apply(kq, name, prec, tol):
     assert np.all(out[pad] == 0.0)
 
 
+@pytest.mark.parametrize("name", ["csr", "csr_multichunk"])
+def test_kkt_apply_staged_operator(kq, name, monkeypatch):
+    """FP32 products of short-row CSR problems normally run the
+    register-streamed operator; KQ_STAGED=1 at create selects the staged
+    shared-memory operator instead.  Both against the oracle."""
+    monkeypatch.setenv("KQ_STAGED", "1")
+    qp, S, st, h = _setup(kq, name, seed=1)
+    monkeypatch.delenv("KQ_STAGED")
+    mu = 0.01
+    r = I.residuals(S, st, mu)
+    dg, D, _, _ = I.reduced_system(S, st, r, mu)
+    v = np.random.default_rng(5).standard_normal(S.NK)
+    ref = I.kkt_apply(S, dg, D, v)
+    out = np.zeros(h.nkp)
+    kq.kkt_apply(h, to_padded(S, v), out, 1)
+    assert relerr(from_padded(S, out), ref) <= 1e-5
+
+
 @pytest.mark.parametrize("prec", [0, 1], ids=["f64", "mixed"])
 @pytest.mark.parametrize("name", list(PROBLEMS))
 def test_kkt_pcg_solve(kq, name, prec):
