@@ -40,6 +40,15 @@ def algo_bytes(qp) -> float:
     return nnz * 8.0 + (rows + 1) * 4.0 + rows * 4.0
 
 
+def stored_bytes(qp) -> float:
+    """Bytes the register-streamed FP32 product reads per K*v: per row, its
+    nonzeros padded to a multiple of 4 (4 B value + 2 B column each) and a
+    16-byte row descriptor."""
+    import numpy as np
+    ln = np.diff(qp.P.indptr)
+    return float(np.sum(4 * ((ln + 3) // 4)) * 6.0 + len(ln) * 16.0)
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
     for f in ("pcg.cu", "common.cuh", "kq_internal.h"):
@@ -185,6 +194,81 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def run_other(args):
+    """Time-to-1e-6 of the other configurations, plain FP64 against mixed
+    (and batched), on one GPU.  One JSON line per form; the median of
+    `--steps` solves after `--warmup` (wall time of ipm_solve, which ends with
+    the status read back on the host)."""
+    import numpy as np
+    import torch
+    import qpgen
+    import paper_2308_00637_gb300 as kq
+    from paper_2308_00637_gb300 import build as kqbuild
+    torch.cuda.set_device(0)
+    kqbuild.build()
+    kq.load()
+    steps, warm = max(1, args.steps), max(0, args.warmup)
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    if args.workload in ("c0", "c2", "c4"):
+        qp = {"c0": qpgen.config0, "c2": qpgen.config2, "c4": qpgen.config4}[args.workload]()
+        for prec, name in ((kq.KQ_PREC_F64, "f64"), (kq.KQ_PREC_MIXED, "mixed")):
+            h = kq.create_from(qp, device_tensors=True)
+            opts = kq.default_ipm_opts(precision=prec)
+            x = np.zeros(qp.n)
+            ts, st = [], None
+            for k in range(warm + steps):
+                _, st = kq.ipm_solve(h, opts, x=x)
+                if k >= warm:
+                    ts.append(st.time_s)
+            d = {"workload": args.workload, "form": name, "time_to_1e-6_s": float(np.median(ts)),
+                 "ipm_iters": st.ipm_iters, "pcg_iters": int(st.pcg_iters),
+                 "pcg_iters_f64": int(st.pcg_iters_f64), "pcg_kernel_ms": st.pcg_kernel_ms,
+                 "objective": qp.objective(x), "n": qp.n}
+            if args.workload == "c4":
+                gbar = qpgen.config4_directions(qp, 1)[0]
+                po = kq.default_pcg_opts(tol=1e-7)
+                tb = []
+                for k in range(warm + steps):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    kq.qp_backward(h, gbar, grad_p=np.zeros(qp.n), grad_lA=np.zeros(qp.m),
+                                   grad_uA=np.zeros(qp.m), opts=po)
+                    torch.cuda.synchronize()
+                    if k >= warm:
+                        tb.append(time.perf_counter() - t0)
+                d["backward_s"] = float(np.median(tb))
+                d["backward_over_forward"] = d["backward_s"] / d["time_to_1e-6_s"]
+            emit(d)
+            kq.qp_destroy(h)
+        return 0
+
+    nqp = 128 if args.workload == "batch128" else 512
+    hi = 1024 if args.workload == "batch128" else 4096
+    sizes = qpgen.batch_sizes(nqp, 64, hi, size_seed=5 if nqp == 128 else 0)
+    qps = [qpgen.batch_qp(k, n, light=True) for k, n in enumerate(sizes)]
+    for prec, name in ((kq.KQ_PREC_MIXED, "batched mixed"), (kq.KQ_PREC_F64, "batched f64")):
+        b = kq.qp_create_batch(qps)
+        xs = [np.zeros(q.n) for q in qps]
+        rc, status, st = kq.ipm_solve_batch(b, kq.default_ipm_opts(precision=prec), xs)
+        emit({"workload": args.workload, "form": name, "time_to_1e-6_s": st.time_s,
+              "converged": st.converged, "nqp": nqp, "pcg_iters": int(st.pcg_iters),
+              "pcg_maxit_hits": st.pcg_maxit_hits, "pcg_kernel_ms": st.pcg_kernel_ms,
+              "sum_n2": int(sum(n * n for n in sizes))})
+        kq.qp_batch_destroy(b)
+    if args.sequential:
+        tot, its = 0.0, 0
+        for q in qps:
+            _, st, _ = kq.solve(q, kq.default_ipm_opts(precision=kq.KQ_PREC_F64))
+            tot += st.time_s
+            its += int(st.pcg_iters)
+        emit({"workload": args.workload, "form": "one at a time f64", "time_to_1e-6_s": tot,
+              "pcg_iters": its, "nqp": nqp})
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -198,9 +282,17 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--write-counts", default=None)
+    ap.add_argument("--workload", default="c1",
+                    choices=["c1", "c0", "c2", "c4", "batch128", "batch512"],
+                    help="c1 (default) is the benchmark; the others print one timing line "
+                         "per form (plain FP64 / mixed / batched) on the other configurations")
+    ap.add_argument("--sequential", action="store_true",
+                    help="batch workloads: also time plain FP64 one QP at a time")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "c1":
+        return run_other(args)
 
     import numpy as np
     import torch
@@ -281,8 +373,17 @@ def main():
     prod = sum(s.pcg_products for s in stats)
     kms = sum(s.pcg_kernel_ms for s in stats)
     launches = sum(s.pcg_launches for s in stats)
+    # the dominant kernel: the FP32 passes in mixed precision (register-streamed
+    # CSR), the FP64 launches in plain FP64
+    if prec == kq.KQ_PREC_MIXED:
+        prod_dom = prod - sum(s.pcg_products_f64 for s in stats)
+        kms_dom = kms - sum(s.pcg_kernel_ms_f64 for s in stats)
+        kname = "pcg_kernel<OpCsrRows, float> (persistent FP32 PCG pass)"
+    else:
+        prod_dom, kms_dom = prod, kms
+        kname = "pcg_kernel<OpCsrStaged, double> (persistent FP64 PCG solve)"
     abytes = algo_bytes(qp)
-    achieved = prod * abytes / (kms * 1e-3) / 1e9
+    achieved = prod_dom * abytes / (kms_dom * 1e-3) / 1e9
     peak, peak_src = read_peaks()
     traffic = None
     try:
@@ -364,14 +465,18 @@ def main():
                        "l2": "inputs larger than L2 (P is 160 MB > 129 MB)",
                        "parallelism": "replicas" if world > 1 else "single-gpu"},
             "ipm_iters": s0.ipm_iters, "pcg_iters": int(s0.pcg_iters),
-            "pcg_products": int(s0.pcg_products), "pcg_maxit_hits": s0.pcg_maxit_hits,
+            "pcg_products": int(s0.pcg_products), "pcg_iters_f64": int(s0.pcg_iters_f64),
+            "pcg_maxit_hits": s0.pcg_maxit_hits,
             "pcg_iters_per_s": s0.pcg_iters / t_step,
             "kkt_rel": met["kkt_rel"], "objective": met["objective"],
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,
-                         "kernel": "pcg_kernel<OpCsrStaged> (persistent PCG solve)",
-                         "algorithmic_bytes_per_product": abytes, "note": ALGO_BYTES_NOTE},
+                         "kernel": kname, "products": int(prod_dom),
+                         "kernel_ms": kms_dom,
+                         "algorithmic_bytes_per_product": abytes, "note": ALGO_BYTES_NOTE,
+                         "stored_bytes_per_product": stored_bytes(qp) if prec == kq.KQ_PREC_MIXED
+                         else abytes},
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(sum(s.kernel_launches for s in stats)),

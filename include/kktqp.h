@@ -119,6 +119,8 @@ typedef struct {
   long long pcg_products;  /* K*v products inside PCG kernels (iterations+applies)*/
   long long kernel_launches; /* all kernels this call launched                   */
   long long pcg_iters_f64; /* MIXED: PCG iterations run in FP64 (rescue passes) */
+  long long pcg_products_f64;  /* products inside FP64 launches (passes + residuals) */
+  double pcg_kernel_ms_f64;    /* device time of the FP64 persistent launches       */
 } kq_ipm_stats;
 
 typedef struct {
@@ -136,6 +138,8 @@ typedef struct {
   double rel_res;          /* true ||rhs - K z|| / ||rhs|| in FP64              */
   double kernel_ms;        /* device time of the persistent kernels             */
   int iters_f64;           /* iterations of FP64 passes (all of them in F64)    */
+  int products_f64;        /* products inside FP64 launches (passes + residuals)*/
+  double kernel_ms_f64;    /* device time of the FP64 persistent launches       */
 } kq_pcg_stats;
 
 /* Fill *o with the paper's settings (gamma 0.99, mu/10, mu_tol 1e-6, PCG tol

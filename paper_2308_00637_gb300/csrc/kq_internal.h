@@ -71,10 +71,11 @@ struct DevKKT {
 struct RowDesc { int32_t off; int32_t a; float w2hi; float w2lo; };
 struct ChunkInfo { int64_t src; int32_t nelem; int32_t desc0; int32_t ndesc; int32_t pad; };
 
-// Register-streamed CSR layout (FP32 products, rows of at most 128 nonzeros).
-// Each row's nonzeros are padded to a multiple of four and stored as groups
-// of four (one 16-byte load of values and one of window-relative columns per
-// lane); slot 4*l + q of a row belongs to lane l, load component q.  The host
+// Register-streamed CSR layout (FP32 products, rows of at most 128 nonzeros,
+// column windows of at most 65536).  Each row's nonzeros are padded to a
+// multiple of four and stored as groups of four (one 16-byte load of values
+// and one 8-byte load of 16-bit window-relative columns per lane); slot
+// 4*l + q of a row belongs to lane l, load component q.  The host
 // permutes a row's nonzeros so that the 32 lanes of one component hit
 // distinct shared-memory banks where the row allows.
 struct RowSlot { int32_t off4; int32_t len4; int32_t a; float w2; };
@@ -123,6 +124,8 @@ struct PcgWork {
   float *accx32 = nullptr;     // n
   double *g64 = nullptr;       // k + me (LOWRANK)
   double *coefA = nullptr;     // m (DENSE column pass)
+  double *dinv = nullptr;      // nkp: 1 / diag(K) of the current solve
+  float *p32_0 = nullptr, *p32_1 = nullptr, *y32 = nullptr;  // nkp FP32 copies (register-streamed CSR)
   double *slots = nullptr;     // 4 * G
   unsigned int *bar = nullptr; // [count, gen]
   int *err = nullptr;          // device error flag
@@ -138,9 +141,9 @@ struct PcgWork {
   bool rows_ok = false;
   RowSlot *rslot = nullptr;    // nP
   float *rval = nullptr;       // 4 * sum(len4)
-  int32_t *rcol = nullptr;     // 4 * sum(len4), relative to the CTA's window start
+  uint16_t *rcol = nullptr;    // 4 * sum(len4), 16-bit offsets from the CTA's window start
   int rws = 0;                 // stride of the per-warp accumulators (floats)
-  int pf_dist = 2;             // L2 prefetch distance in warp steps
+  int pf_dist = 0;             // L2 prefetch distance in warp steps (0: off)
   size_t smem_rows = 0;
   int64_t *row_begin = nullptr;   // G+1 partition of rows (P rows / dense rows)
   int32_t *win_lo = nullptr, *win_hi = nullptr;  // G column windows (CSR)

@@ -61,9 +61,11 @@ struct PcgArgs {
   // register-streamed CSR (FP32 products)
   const RowSlot *rslot;
   const float4 *rval4;
-  const int4 *rcol4;
+  const uint2 *rcol2;           // four 16-bit window-relative columns per lane
   int rws;                      // per-warp accumulator stride (floats, multiple of 32)
-  int pf_dist;                  // L2 prefetch distance in warp steps (0: off)
+  int pf_dist;                  // L2 prefetch distance in warp steps (0: off, the default)
+  double *dinv;                 // 1 / diag(K), formed at the start of a solve (or null)
+  float *p32_0, *p32_1, *y32;   // FP32 copies of p (paired with pb0 / pb1) and y (or null)
 };
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
@@ -83,18 +85,106 @@ __device__ __forceinline__ double sum_slots(const double *s, int G, double *sh) 
   return v;
 }
 
+// Two slot sums in one pass (same order as sum_slots).
+__device__ __forceinline__ void sum_slots2(const double *s0, const double *s1, int G, double *sh,
+                                           double &o0, double &o1) {
+  if (threadIdx.x < 32) {
+    double v0 = 0.0, v1 = 0.0;
+    for (int i = threadIdx.x; i < G; i += 32) {
+      v0 += __ldcg(s0 + i);
+      v1 += __ldcg(s1 + i);
+    }
+    v0 = warp_sum(v0);
+    v1 = warp_sum(v1);
+    if (threadIdx.x == 0) { sh[0] = v0; sh[1] = v1; }
+  }
+  __syncthreads();
+  o0 = sh[0];
+  o1 = sh[1];
+  __syncthreads();
+}
+
+// Threads that update the owned vector entries: one entry per thread where
+// the block allows, on as few warps as that takes.  The SM's FP64 pipe is
+// narrow, so warps without entries stay out of the FP64 reductions.
+__device__ __forceinline__ int vec_threads(int64_t owned) {
+  int64_t w = (owned + 31) & ~(int64_t)31;
+  if (w < 32) w = 32;
+  if (w > (int64_t)blockDim.x) w = blockDim.x;
+  return (int)w;
+}
+
+// FP32 copy of p paired with a given FP64 buffer (null when not kept)
+__device__ __forceinline__ float *p32_of(const PcgArgs &a, const double *pbuf) {
+  if (!a.p32_0) return nullptr;
+  return pbuf == a.pb0 ? a.p32_0 : a.p32_1;
+}
+
 // p_new for this CTA's owned vector entries; returns sum dg_j p_j^2 (x part)
 __device__ __forceinline__ double write_owned_p(const PcgArgs &a, const double *ysrc,
                                                 const double *pold, double *pnew, double beta,
                                                 int64_t vb, int64_t ve) {
   double pq = 0.0;
   const int64_t n = a.P.n;
-  for (int64_t i = vb + threadIdx.x; i < ve; i += blockDim.x) {
-    double pi = ldcg(ysrc + i) + beta * ldcg(pold + i);
-    pnew[i] = pi;
-    if (i < n) pq += a.dg[i] * pi * pi;
+  const int vt = vec_threads(ve - vb);
+  float *p32 = a.apply ? nullptr : p32_of(a, pnew);
+  if ((int)threadIdx.x < vt) {
+    for (int64_t i = vb + threadIdx.x; i < ve; i += vt) {
+      double pi = ldcg(ysrc + i) + beta * ldcg(pold + i);
+      pnew[i] = pi;
+      if (p32) p32[i] = (float)pi;
+      if (i < n) pq += a.dg[i] * pi * pi;
+    }
   }
   return pq;
+}
+
+// Sum over the vector threads (warps 0 .. vt/32-1) of NV doubles; result in
+// thread 0.  All threads must call.
+template <int NV>
+__device__ __forceinline__ void vec_sum(double (&v)[NV], double *sh, int vt) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nwv = (vt + 31) >> 5;
+  if (wid < nwv) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+    if (lane == 0) {
+#pragma unroll
+      for (int k = 0; k < NV; ++k) sh[k * 32 + wid] = v[k];
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      double t = 0.0;
+      for (int w = 0; w < nwv; ++w) t += sh[k * 32 + w];
+      v[k] = t;
+    }
+  }
+  __syncthreads();
+}
+
+// Block sum of one double held by any thread, through a shared buffer of
+// blockDim doubles: four warps add a quarter each, thread 0 the four partials.
+__device__ __forceinline__ double block_sum_buf(double v, double *buf, double *sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nt = blockDim.x;
+  buf[threadIdx.x] = v;
+  __syncthreads();
+  const int np = min(4, (nt + 31) >> 5), nq = (nt + np - 1) / np;
+  if (wid < np) {
+    double t = 0.0;
+    for (int j = wid * nq + lane; j < min(nt, (wid + 1) * nq); j += 32) t += buf[j];
+    t = warp_sum(t);
+    if (lane == 0) sh[wid] = t;
+  }
+  __syncthreads();
+  double r = 0.0;
+  if (threadIdx.x == 0)
+    for (int w = 0; w < np; ++w) r += sh[w];
+  __syncthreads();
+  return r;
 }
 
 // ---------------------------------------------------------------- CSR (H = P'W2P, A = rows of P)
@@ -915,49 +1005,27 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
 }
 
 // Every warp walks its own rows (pairs 2w, 2w+1, then +2 NW, ...) with plain
-// 16-byte loads straight into registers, the next pair's loads in flight
-// while the current pair is processed; thread 0 prefetches the CTA's rows a
-// few warp steps ahead into L2.  No shared-memory staging and no CTA barrier
-// inside the product.  The scatter goes into the warp's private accumulator
+// 16-byte loads straight into registers, two pairs' loads in flight while the
+// current pair is processed (optionally, KQ_PF > 0, thread 0 also prefetches
+// the CTA's rows into L2; measured slower on the dose QP, so off by default).
+// No shared-memory staging and no CTA barrier inside the product.  The scatter goes into the warp's private accumulator
 // with plain read-modify-write: the columns of one row are distinct (padding
 // included), and __syncwarp orders the rows of a warp.  The private copies
 // are summed once per product.
 struct OpCsrRows {
-  struct Pair { RowSlot s0, s1; float4 v0, v1; int4 c0, c1; };
-
-  static __device__ __forceinline__ void load_pair(const PcgArgs &a, const RowSlot *S, int i,
-                                                   int nr, int lane, Pair &q) {
-    const float4 fz = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int4 iz = make_int4(0, 0, 0, 0);
-    q.s0 = RowSlot{0, 0, -1, 0.f};
-    q.s1 = RowSlot{0, 0, -1, 0.f};
-    q.v0 = fz; q.v1 = fz; q.c0 = iz; q.c1 = iz;
-    if (i < nr) {
-      q.s0 = S[i];
-      if (lane < q.s0.len4) {
-        q.v0 = __ldcs(a.rval4 + q.s0.off4 + lane);
-        q.c0 = __ldcs(a.rcol4 + q.s0.off4 + lane);
-      }
-    }
-    if (i + 1 < nr) {
-      q.s1 = S[i + 1];
-      if (lane < q.s1.len4) {
-        q.v1 = __ldcs(a.rval4 + q.s1.off4 + lane);
-        q.c1 = __ldcs(a.rcol4 + q.s1.off4 + lane);
-      }
-    }
+  // The CTA's rows occupy the contiguous lane-group range [base, end); the L2
+  // prefetch cuts it into one piece per warp step (no loads needed to find it).
+  static __device__ __forceinline__ int *pf_state() {
+    __shared__ int s_pf[3];   // base, end, groups per step
+    return s_pf;
   }
-
-  // thread 0: L2 prefetch of warp step `step` (rows [step*2nw, (step+1)*2nw))
-  static __device__ __forceinline__ void prefetch_step(const PcgArgs &a, const RowSlot *S, int step,
-                                                       int nr, int nw) {
-    const int r0 = step * 2 * nw;
-    if (r0 >= nr) return;
-    const int r1 = min(nr, r0 + 2 * nw) - 1;
-    const RowSlot f = S[r0], l = S[r1];
-    const uint32_t bytes = (uint32_t)(l.off4 + l.len4 - f.off4) * 16u;
-    prefetch_l2(a.rval4 + f.off4, bytes);
-    prefetch_l2(a.rcol4 + f.off4, bytes);
+  // thread 0: L2 prefetch of the piece of warp step `step`
+  static __device__ __forceinline__ void prefetch_step(const PcgArgs &a, int step) {
+    const int *st = pf_state();
+    const int b = st[0] + step * st[2], e = min(st[1], b + st[2]);
+    if (b >= e) return;
+    prefetch_l2(a.rval4 + b, (uint32_t)(e - b) * 16u);
+    prefetch_l2(a.rcol2 + b, (uint32_t)(e - b) * 8u);
   }
 
   template <class T>
@@ -980,10 +1048,20 @@ struct OpCsrRows {
       aDu[i] = (float)a.Du[ai];
       afl[i] = (uint8_t)((a.P.hasl[ai] ? 1 : 0) | (a.P.hasu[ai] ? 2 : 0));
     }
-    if (tid == 0 && a.pf_dist > 0) {
+    if (tid == 0) {
       const int64_t r0 = a.row_begin[cta];
       const int nr = (int)(a.row_begin[cta + 1] - r0);
-      for (int s = 0; s < a.pf_dist; ++s) prefetch_step(a, a.rslot + r0, s, nr, nw);
+      int *st = pf_state();
+      st[0] = st[1] = st[2] = 0;
+      if (nr > 0) {
+        const RowSlot f = a.rslot[r0], l = a.rslot[r0 + nr - 1];
+        const int nsteps = (nr + 2 * nw - 1) / (2 * nw);
+        st[0] = f.off4;
+        st[1] = l.off4 + l.len4;
+        st[2] = (st[1] - st[0] + nsteps - 1) / nsteps;
+      }
+      if (a.pf_dist > 0)
+        for (int s = 0; s < a.pf_dist; ++s) prefetch_step(a, s);
     }
     __syncthreads();
   }
@@ -1027,51 +1105,105 @@ struct OpCsrRows {
     const int64_t r0 = a.row_begin[cta];
     const int nr = (int)(a.row_begin[cta + 1] - r0);
     const RowSlot *S = a.rslot + r0;
-    // the first pair's loads do not depend on p: start them before the window
-    Pair cur;
-    int i = 2 * warp;
-    load_pair(a, S, i, nr, lane, cur);
-    double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
-    for (int j = tid; j < wlen; j += blockDim.x) {
-      const int c = lo + j;
-      pw[j] = (float)(ldcg(ysrc + c) + beta * ldcg(pold + c));
-    }
-    for (int k = tid; k < na; k += blockDim.x) {
-      const int ai = alo + k;
-      apl[k] = (float)((afl[k] & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0);
-      apu[k] = (float)((afl[k] & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0);
-    }
-    __syncthreads();
+    // Loads run ahead of the arithmetic: slot descriptors three pair-steps
+    // ahead, values and columns two; the first steps do not depend on p and
+    // start before the window is filled.
+    auto ld_slots = [&](int ii, RowSlot &x0, RowSlot &x1) {
+      x0 = RowSlot{0, 0, -1, 0.f};
+      x1 = RowSlot{0, 0, -1, 0.f};
+      if (ii < nr) x0 = S[ii];
+      if (ii + 1 < nr) x1 = S[ii + 1];
+    };
+    auto ld_data = [&](const RowSlot &x0, const RowSlot &x1, float4 &v0, float4 &v1, uint2 &c0,
+                       uint2 &c1) {
+      v0 = make_float4(0.f, 0.f, 0.f, 0.f);
+      v1 = v0;
+      c0 = make_uint2(0u, 0u);
+      c1 = c0;
+      if (lane < x0.len4) { v0 = __ldcs(a.rval4 + x0.off4 + lane); c0 = __ldcs(a.rcol2 + x0.off4 + lane); }
+      if (lane < x1.len4) { v1 = __ldcs(a.rval4 + x1.off4 + lane); c1 = __ldcs(a.rcol2 + x1.off4 + lane); }
+    };
     float pqt = 0.f;
-    int step = 0;
-    for (; i < nr; i += 2 * nw, ++step) {
-      if (tid == 0 && a.pf_dist > 0) prefetch_step(a, S, step + a.pf_dist, nr, nw);
-      Pair nxt;
-      load_pair(a, S, i + 2 * nw, nr, lane, nxt);
-      const bool act0 = lane < cur.s0.len4, act1 = lane < cur.s1.len4;
+    // one pair of rows: dots with the window, coefficients, scatter
+    auto process = [&](int ii, const RowSlot &s0, const RowSlot &s1, const float4 &v0,
+                       const float4 &v1, const uint2 &p0, const uint2 &p1) {
+      const int4 c0 = make_int4((int)(p0.x & 0xffffu), (int)(p0.x >> 16), (int)(p0.y & 0xffffu),
+                                (int)(p0.y >> 16));
+      const int4 c1 = make_int4((int)(p1.x & 0xffffu), (int)(p1.x >> 16), (int)(p1.y & 0xffffu),
+                                (int)(p1.y >> 16));
+      const bool has1 = ii + 1 < nr;
+      const bool act0 = lane < s0.len4, act1 = lane < s1.len4;
       float d0 = 0.f, d1 = 0.f;
-      if (act0)
-        d0 = cur.v0.x * pw[cur.c0.x] + cur.v0.y * pw[cur.c0.y] + cur.v0.z * pw[cur.c0.z] +
-             cur.v0.w * pw[cur.c0.w];
-      if (act1)
-        d1 = cur.v1.x * pw[cur.c1.x] + cur.v1.y * pw[cur.c1.y] + cur.v1.z * pw[cur.c1.z] +
-             cur.v1.w * pw[cur.c1.w];
+      if (act0) d0 = v0.x * pw[c0.x] + v0.y * pw[c0.y] + v0.z * pw[c0.z] + v0.w * pw[c0.w];
+      if (act1) d1 = v1.x * pw[c1.x] + v1.y * pw[c1.y] + v1.z * pw[c1.z] + v1.w * pw[c1.w];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         d0 += __shfl_xor_sync(0xffffffffu, d0, o);
         d1 += __shfl_xor_sync(0xffffffffu, d1, o);
       }
-      const RowDesc rd0{0, cur.s0.a, cur.s0.w2, 0.f}, rd1{0, cur.s1.a, cur.s1.w2, 0.f};
-      const float u0 = OpCsrStaged::row_coef<float>(a, rd0, d0, ysrc, pold, beta, alo, na, arho, acs,
-                                                    aDl, aDu, apl, apu, afl, lane, pqt);
+      const RowDesc rd0{0, s0.a, s0.w2, 0.f}, rd1{0, s1.a, s1.w2, 0.f};
+      const float u0 = OpCsrStaged::row_coef<float>(a, rd0, d0, ysrc, pold, beta, alo, na, arho,
+                                                    acs, aDl, aDu, apl, apu, afl, lane, pqt);
       float u1 = 0.f;
-      if (i + 1 < nr)
+      if (has1)
         u1 = OpCsrStaged::row_coef<float>(a, rd1, d1, ysrc, pold, beta, alo, na, arho, acs, aDl,
                                           aDu, apl, apu, afl, lane, pqt);
       if (lane == 0) pqt += u0 * d0 + u1 * d1;
-      scatter(accw, cur.v0, cur.c0, u0, act0);
-      scatter(accw, cur.v1, cur.c1, u1, act1);
-      cur = nxt;
+      scatter(accw, v0, c0, u0, act0);
+      scatter(accw, v1, c1, u1, act1);
+    };
+    int i = 2 * warp;
+    const int stp = 2 * nw;
+    RowSlot sa0, sa1, sb0, sb1, sc0, sc1;
+    float4 va0, va1, vb0, vb1;
+    uint2 ca0, ca1, cb0, cb1;
+    ld_slots(i, sa0, sa1);
+    ld_slots(i + stp, sb0, sb1);
+    ld_slots(i + 2 * stp, sc0, sc1);
+    double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
+    ld_data(sa0, sa1, va0, va1, ca0, ca1);
+    ld_data(sb0, sb1, vb0, vb1, cb0, cb1);
+    const float *p32o = a.apply ? nullptr : p32_of(a, pold);
+    if (p32o && a.y32) {
+      // window p from the FP32 copies of y and p_old (FP32 arithmetic: the
+      // product rounds p to FP32 anyway)
+      const float b32 = (float)beta;
+      // one index space: window columns, then the A rows' lower and upper entries
+      for (int j = tid; j < wlen + 2 * na; j += blockDim.x) {
+        if (j < wlen) {
+          const int c = lo + j;
+          pw[j] = fmaf(b32, __ldcg(p32o + c), __ldcg(a.y32 + c));
+        } else {
+          const int k = (j - wlen) >> 1, up = (j - wlen) & 1;
+          const int64_t ix = (up ? up_off : lo_off) + alo + k;
+          const float v = (afl[k] & (up ? 2 : 1)) ? fmaf(b32, __ldcg(p32o + ix), __ldcg(a.y32 + ix)) : 0.f;
+          if (up) apu[k] = v; else apl[k] = v;
+        }
+      }
+    } else {
+      for (int j = tid; j < wlen; j += blockDim.x) {
+        const int c = lo + j;
+        pw[j] = (float)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+      }
+      for (int k = tid; k < na; k += blockDim.x) {
+        const int ai = alo + k;
+        apl[k] = (float)((afl[k] & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0);
+        apu[k] = (float)((afl[k] & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0);
+      }
+    }
+    __syncthreads();
+    int step = 0;
+    for (; i < nr; i += stp, ++step) {
+      if (tid == 0 && a.pf_dist > 0) prefetch_step(a, step + a.pf_dist);
+      RowSlot sd0, sd1;
+      float4 vc0, vc1;
+      uint2 cc0, cc1;
+      ld_slots(i + 3 * stp, sd0, sd1);
+      ld_data(sc0, sc1, vc0, vc1, cc0, cc1);
+      process(i, sa0, sa1, va0, va1, ca0, ca1);
+      sa0 = sb0; sa1 = sb1; sb0 = sc0; sb1 = sc1; sc0 = sd0; sc1 = sd1;
+      va0 = vb0; va1 = vb1; ca0 = cb0; ca1 = cb1;
+      vb0 = vc0; vb1 = vc1; cb0 = cc0; cb1 = cc1;
     }
     __syncthreads();
     // sum the private copies into the global accumulator; zero them
@@ -1085,14 +1217,20 @@ struct OpCsrRows {
         acc4[(size_t)w * ws4 + j4] = make_float4(0.f, 0.f, 0.f, 0.f);
       }
       const int c = 4 * j4;
-      if (c + 0 < wlen && t.x != 0.f) atomicAdd(accg + lo + c + 0, t.x);
-      if (c + 1 < wlen && t.y != 0.f) atomicAdd(accg + lo + c + 1, t.y);
-      if (c + 2 < wlen && t.z != 0.f) atomicAdd(accg + lo + c + 2, t.z);
-      if (c + 3 < wlen && t.w != 0.f) atomicAdd(accg + lo + c + 3, t.w);
+      if (c + 3 < wlen) {
+        // lo is a multiple of 4: one 16-byte vector reduction
+        if (t.x != 0.f || t.y != 0.f || t.z != 0.f || t.w != 0.f)
+          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(accg + lo + c),
+                       "f"(t.x), "f"(t.y), "f"(t.z), "f"(t.w) : "memory");
+      } else {
+        if (c + 0 < wlen && t.x != 0.f) atomicAdd(accg + lo + c + 0, t.x);
+        if (c + 1 < wlen && t.y != 0.f) atomicAdd(accg + lo + c + 1, t.y);
+        if (c + 2 < wlen && t.z != 0.f) atomicAdd(accg + lo + c + 2, t.z);
+      }
     }
     // prefetch the first steps of the next product (the matrix does not change)
     if (tid == 0 && a.pf_dist > 0)
-      for (int s2 = 0; s2 < a.pf_dist; ++s2) prefetch_step(a, S, s2, nr, nw);
+      for (int s2 = 0; s2 < a.pf_dist; ++s2) prefetch_step(a, s2);
     (void)ok;
     return pq + (double)pqt;
   }
@@ -1126,18 +1264,51 @@ __device__ __forceinline__ double run_phaseA(const PcgArgs &a, const double *ysr
 
 // The PCG solve (or one product in APPLY mode) of one problem by the CTAs
 // cta = 0..G-1 (the whole grid, or one team of the batched solver).
+// Sum of G slot values by warp 0 in a fixed order, the loads of up to 160
+// slots issued together (one memory round trip).
+__device__ __forceinline__ double slot_sum_w0(const double *s, int G) {
+  double v = 0.0;
+  for (int b = 0; b < G; b += 160) {
+    double t[5];
+#pragma unroll
+    for (int k = 0; k < 5; ++k) {
+      const int i = b + threadIdx.x + 32 * k;
+      t[k] = (i < G) ? __ldcg(s + i) : 0.0;
+    }
+    v += ((t[0] + t[1]) + (t[2] + t[3])) + t[4];
+  }
+  return warp_sum(v);
+}
+
+// Sum of two slot arrays by warp 0 (fixed order); result in warp 0.
+__device__ __forceinline__ void slots2_t0(const double *s0, const double *s1, int G, double &o0,
+                                          double &o1) {
+  if (threadIdx.x < 32) {
+    o0 = slot_sum_w0(s0, G);
+    o1 = slot_sum_w0(s1, G);
+  }
+}
+
+// The PCG solve (or one product in APPLY mode) of one problem by the CTAs
+// cta = 0..G-1 (the whole grid, or one team of the batched solver).  The
+// scalar recurrence (rho, alpha, beta, the stopping tests) runs in thread 0
+// and reaches the other threads through shared memory: FP64 arithmetic is
+// scarce on this SM, so it is not repeated by every warp.
 template <class OP, class T>
 __device__ void pcg_body(const PcgArgs &a, const int cta, const int G, unsigned char *smem,
-                         double *sh) {
+                         double *sh, double *sbuf) {
   const int tid = threadIdx.x;
   const int64_t nkp = a.P.nkp, n = a.P.n;
   const int64_t chunk = ceil_div64(nkp, G);
   const int64_t vb = min(nkp, (int64_t)cta * chunk), ve = min(nkp, vb + chunk);
+  const int vt = vec_threads(ve - vb);
   T *accg = reinterpret_cast<T *>(a.accx);
   double *pold = a.pb0, *pnew = a.pb1;
-  double beta = 0.0, rho = 0.0, bb = 0.0, rr = 0.0;
+  double beta = 0.0;
+  // thread 0's scalars
+  double rho = 0.0, bb = 0.0, rr = 0.0, rr_mark = 0.0;
   int it = 0;
-  bool ok = true;
+  bool ok = true, stop = false;
   const double *ysrc = a.apply ? a.rhs : a.y;
   PipeState ps;
   if constexpr (IsStaged<OP>::value) OP::template begin<T>(a, smem, ps);
@@ -1146,90 +1317,126 @@ __device__ void pcg_body(const PcgArgs &a, const int cta, const int G, unsigned 
   // ---- initialisation: z = 0, r = rhs, y = r / diag, p_old = 0
   {
     double part[2] = {0.0, 0.0};
-    for (int64_t i = vb + tid; i < ve; i += blockDim.x) {
-      pold[i] = 0.0;
-      if (i < n) accg[i] = (T)0;
-      if (!a.apply) {
-        const double ri = a.rhs[i];
-        const double yi = ri / a.diag[i];
-        a.z[i] = 0.0;
-        a.r[i] = ri;
-        a.y[i] = yi;
-        part[0] += ri * ri;
-        part[1] += ri * yi;
+    if (tid < vt) {
+      for (int64_t i = vb + tid; i < ve; i += vt) {
+        pold[i] = 0.0;
+        if (a.p32_0) a.p32_0[i] = 0.f;
+        if (i < n) accg[i] = (T)0;
+        if (!a.apply) {
+          const double ri = a.rhs[i];
+          const double di = 1.0 / a.diag[i];
+          if (a.dinv) a.dinv[i] = di;
+          const double yi = ri * di;
+          a.z[i] = 0.0;
+          a.r[i] = ri;
+          a.y[i] = yi;
+          if (a.y32) a.y32[i] = (float)yi;
+          part[0] += ri * ri;
+          part[1] += ri * yi;
+        }
       }
     }
     if (cta == 0 && a.g)
       for (int64_t c = tid; c < a.P.k + a.P.me; c += blockDim.x) a.g[c] = 0.0;
-    block_sum<2>(part, sh);
+    vec_sum<2>(part, sh, vt);
     if (tid == 0) { a.slots[cta] = part[0]; a.slots[G + cta] = part[1]; }
   }
   ok = grid_sync(a.bar);
   if (ok && !a.apply) {
-    bb = sum_slots(a.slots, G, sh);
-    rho = sum_slots(a.slots + G, G, sh);
-    rr = bb;
-  }
-  double rr_mark = bb;
-  while (ok) {
-    if (!a.apply && (rr <= a.tol2 * bb || it >= a.maxit)) break;
-    // FP32 correction passes: hand over to the FP64 pass once they stagnate
-    if (a.stag_window > 0 && it > 0 && it % a.stag_window == 0) {
-      if (rr > 0.25 * rr_mark) break;
-      rr_mark = rr;
+    slots2_t0(a.slots, a.slots + G, G, bb, rho);
+    if (tid == 0) {
+      rr = bb;
+      rr_mark = bb;
+      sh[0] = (rr <= a.tol2 * bb || a.maxit <= 0) ? 1.0 : 0.0;
     }
+    __syncthreads();
+    stop = sh[0] != 0.0;
+    __syncthreads();
+  }
+  while (ok) {
+    if (!a.apply && stop) break;
     // ---- phase A: q = K p,  p = y + beta p_old
     double pq = run_phaseA<OP, T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ps, ok, cta, G);
     if (!ok) break;
-    {
-      double v1[1] = {pq};
-      block_sum<1>(v1, sh);
-      if (tid == 0) a.slots[2 * G + cta] = v1[0];
-    }
+    pq = block_sum_buf(pq, sbuf, sh);
+    if (tid == 0) a.slots[2 * G + cta] = pq;
     ok = grid_sync(a.bar);
     if (!ok) break;
     if (a.apply) {
-      for (int64_t i = vb + tid; i < ve; i += blockDim.x) {
-        const double pi = pnew[i];
-        a.z[i] = (i < n) ? (double)__ldcg(accg + i) + a.dg[i] * pi : __ldcg(a.qlam + (i - n));
-      }
+      if (tid < vt)
+        for (int64_t i = vb + tid; i < ve; i += vt) {
+          const double pi = pnew[i];
+          a.z[i] = (i < n) ? (double)__ldcg(accg + i) + a.dg[i] * pi : __ldcg(a.qlam + (i - n));
+        }
       break;
     }
-    const double pqt = sum_slots(a.slots + 2 * G, G, sh);
-    if (!(pqt > 0.0)) {
-      if (tid == 0 && cta == 0) atomicCAS(a.bar.err, 0, isnan(pqt) ? 8 : 4);
-      break;
-    }
-    const double alpha = rho / pqt;
-    // ---- phase C: vector updates on owned entries
-    double part[2] = {0.0, 0.0};
-    for (int64_t i = vb + tid; i < ve; i += blockDim.x) {
-      const double pi = pnew[i];
-      double qi;
-      if (i < n) {
-        qi = (double)__ldcg(accg + i) + a.dg[i] * pi;
-        accg[i] = (T)0;
-      } else {
-        qi = __ldcg(a.qlam + (i - n));
+    // alpha = rho / p'Kp (thread 0)
+    {
+      double pqt = 0.0, unused = 0.0;
+      if (tid < 32) pqt = slot_sum_w0(a.slots + 2 * G, G);
+      (void)unused;
+      if (tid == 0) {
+        const int bad = (pqt > 0.0) ? 0 : (isnan(pqt) ? 8 : 4);
+        if (bad && cta == 0) atomicCAS(a.bar.err, 0, bad);
+        sh[0] = bad ? 0.0 : rho / pqt;
+        sh[1] = (double)bad;
       }
-      a.z[i] += alpha * pi;
-      const double ri = a.r[i] - alpha * qi;
-      a.r[i] = ri;
-      const double yi = ri / a.diag[i];
-      a.y[i] = yi;
-      part[0] += ri * ri;
-      part[1] += ri * yi;
+      __syncthreads();
+      const double alpha = sh[0];
+      const bool bad = sh[1] != 0.0;
+      __syncthreads();
+      if (bad) break;
+      // ---- phase C: vector updates on owned entries
+      double part[2] = {0.0, 0.0};
+      if (tid < vt) {
+        for (int64_t i = vb + tid; i < ve; i += vt) {
+          const double pi = pnew[i];
+          double qi;
+          if (i < n) {
+            qi = (double)__ldcg(accg + i) + a.dg[i] * pi;
+            accg[i] = (T)0;
+          } else {
+            qi = __ldcg(a.qlam + (i - n));
+          }
+          a.z[i] += alpha * pi;
+          const double ri = a.r[i] - alpha * qi;
+          a.r[i] = ri;
+          const double yi = a.dinv ? ri * a.dinv[i] : ri / a.diag[i];
+          a.y[i] = yi;
+          if (a.y32) a.y32[i] = (float)yi;
+          part[0] += ri * ri;
+          part[1] += ri * yi;
+        }
+      }
+      if (cta == 0 && a.g)
+        for (int64_t c = tid; c < a.P.k + a.P.me; c += blockDim.x) a.g[c] = 0.0;
+      vec_sum<2>(part, sh, vt);
+      if (tid == 0) { a.slots[cta] = part[0]; a.slots[G + cta] = part[1]; }
     }
-    if (cta == 0 && a.g)
-      for (int64_t c = tid; c < a.P.k + a.P.me; c += blockDim.x) a.g[c] = 0.0;
-    block_sum<2>(part, sh);
-    if (tid == 0) { a.slots[cta] = part[0]; a.slots[G + cta] = part[1]; }
     ok = grid_sync(a.bar);
     if (!ok) break;
-    rr = sum_slots(a.slots, G, sh);
-    const double rho_new = sum_slots(a.slots + G, G, sh);
-    beta = rho_new / rho;
-    rho = rho_new;
+    // beta and the stopping tests (thread 0)
+    {
+      double rho_new = 0.0, rrn = 0.0;
+      slots2_t0(a.slots, a.slots + G, G, rrn, rho_new);
+      if (tid == 0) {
+        rr = rrn;
+        const double bt = rho_new / rho;
+        rho = rho_new;
+        bool st = rr <= a.tol2 * bb || it + 1 >= a.maxit;
+        // FP32 correction passes: hand over to the FP64 pass once they stagnate
+        if (!st && a.stag_window > 0 && (it + 1) % a.stag_window == 0) {
+          if (rr > 0.25 * rr_mark) st = true;
+          rr_mark = rr;
+        }
+        sh[0] = bt;
+        sh[1] = st ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      beta = sh[0];
+      stop = sh[1] != 0.0;
+      __syncthreads();
+    }
     double *t = pold; pold = pnew; pnew = t;
     ++it;
   }
@@ -1245,7 +1452,8 @@ template <class OP, class T>
 __global__ void __launch_bounds__(512, 1) pcg_kernel(PcgArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sh[32 * 2];
-  pcg_body<OP, T>(a, blockIdx.x, gridDim.x, smem, sh);
+  __shared__ double sbuf[512];
+  pcg_body<OP, T>(a, blockIdx.x, gridDim.x, smem, sh, sbuf);
 }
 
 // Batched dense PCG: CTA b belongs to team cta_team[b]; a team works through
@@ -1260,10 +1468,11 @@ __global__ void __launch_bounds__(512, 1) pcg_batch_kernel(const PcgArgs *__rest
                                                             const int *__restrict__ team_qps) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sh[32 * 2];
+  __shared__ double sbuf[512];
   const TeamInfo ti = teams[cta_team[blockIdx.x]];
   const int rank = blockIdx.x - ti.first_cta;
   for (int q = ti.qp_begin; q < ti.qp_end; ++q) {
-    pcg_body<OpDense<HS, AS>, T>(args[team_qps[q]], rank, ti.size, smem, sh);
+    pcg_body<OpDense<HS, AS>, T>(args[team_qps[q]], rank, ti.size, smem, sh, sbuf);
     __syncthreads();
   }
 }
@@ -1383,14 +1592,16 @@ kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double t
   a.coefA = W.coefA;
   a.rslot = W.rslot;
   a.rval4 = reinterpret_cast<const float4 *>(W.rval);
-  a.rcol4 = reinterpret_cast<const int4 *>(W.rcol);
+  a.rcol2 = reinterpret_cast<const uint2 *>(W.rcol);
   a.rws = W.rws;
   a.pf_dist = W.pf_dist;
   KFun f = prec == KQ_PREC_MIXED ? pick_kernel<float>(h->P) : pick_kernel<double>(h->P);
   size_t smem = W.smem;
+  a.dinv = W.dinv;
   if (prec == KQ_PREC_MIXED && W.rows_ok) {
     f = pcg_kernel<OpCsrRows, float>;
     smem = W.smem_rows;
+    a.p32_0 = W.p32_0; a.p32_1 = W.p32_1; a.y32 = W.y32;
   }
   KQ_CUDA(h, cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
@@ -1623,6 +1834,7 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
     a.stages = 2; a.producer = 0; a.copy_piece = 16;
     a.stag_window = (prec == KQ_PREC_MIXED && !apply) ? 200 : 0;
     a.coefA = W.coefA;
+    a.dinv = W.dinv;
     smem = std::max(smem, (size_t)2 * a.win_cap * (prec == KQ_PREC_MIXED ? sizeof(float) : sizeof(double)));
     if (cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) { err = "memset"; return KQ_ERR_CUDA; }
   }
@@ -1702,7 +1914,7 @@ double pcg_last_kernel_ms() { return g_last_ms; }
 __global__ void k_rows_fill(const int64_t *rowptr, const int32_t *col, const float *val,
                             const RowSlot *slots, const int64_t *row_begin,
                             const int32_t *win_lo, const int32_t *win_hi, int G, int64_t nP,
-                            float *rv, int32_t *rc, int *err) {
+                            float *rv, uint16_t *rc, int *err) {
   __shared__ int s_key[8][128];
   __shared__ int s_rel[8][128];
   __shared__ int s_cnt[8][32];
@@ -1740,7 +1952,7 @@ __global__ void k_rows_fill(const int64_t *rowptr, const int32_t *col, const flo
       for (int j = 0; j < len; ++j) rank += s_key[wib][j] < key;
       const int q = rank & 3, ln = rank >> 2;
       rv[base + 4 * ln + q] = val[s0 + e];
-      rc[base + 4 * ln + q] = s_rel[wib][e];
+      rc[base + 4 * ln + q] = (uint16_t)s_rel[wib][e];
       used[q] |= 1u << (s_rel[wib][e] & 31);
     }
 #pragma unroll
@@ -1766,7 +1978,7 @@ __global__ void k_rows_fill(const int64_t *rowptr, const int32_t *col, const flo
       }
       if (lane == 0) {
         rv[base + 4 * ln + q] = 0.f;
-        rc[base + 4 * ln + q] = pick;
+        rc[base + 4 * ln + q] = (uint16_t)pick;
         s_rel[wib][nrow] = pick;
       }
       used[q] |= 1u << (pick & 31);
@@ -1791,6 +2003,7 @@ bool build_rows_layout(kq_problem *h, int G, int threads, const std::vector<int6
   const int64_t nP = P.nP;
   int wmax = 1;
   for (int c = 0; c < G; ++c) wmax = std::max(wmax, hi[c] - lo[c]);
+  if (wmax > 65536) return false;     // columns are stored as 16-bit window offsets
   const int rws = (wmax + 31) & ~31;
   const int nw = threads / 32;
   const size_t smem = rows_layout(rws, nw, W.a_cap).total;
@@ -1809,7 +2022,7 @@ bool build_rows_layout(kq_problem *h, int G, int threads, const std::vector<int6
   }
   W.rslot = dalloc<RowSlot>(h, slots.size());
   W.rval = dalloc<float>(h, 4 * (tot4 + 1));
-  W.rcol = dalloc<int32_t>(h, 4 * (tot4 + 1));
+  W.rcol = dalloc<uint16_t>(h, 4 * (tot4 + 1));
   int *d_err = dalloc<int>(h, 1);
   if (!W.rslot || !W.rval || !W.rcol || !d_err) return false;
   if (cudaMemcpy(W.rslot, slots.data(), slots.size() * sizeof(RowSlot), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1830,7 +2043,7 @@ bool build_rows_layout(kq_problem *h, int G, int threads, const std::vector<int6
   W.smem_rows = smem;
   {
     const char *pf = getenv("KQ_PF");
-    W.pf_dist = pf ? std::max(0, atoi(pf)) : 2;
+    W.pf_dist = pf ? std::max(0, atoi(pf)) : 0;
   }
   return true;
 }
@@ -1889,6 +2102,9 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
     KQ_CUDA(h, cudaMemcpyAsync(lo.data(), W.win_lo, G * 4, cudaMemcpyDeviceToHost, h->stream));
     KQ_CUDA(h, cudaMemcpyAsync(hi.data(), W.win_hi, G * 4, cudaMemcpyDeviceToHost, h->stream));
     KQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    // window starts on a multiple of 4 columns (16-byte aligned flushes)
+    for (int c = 0; c < G; ++c) lo[c] &= ~3;
+    KQ_CUDA(h, cudaMemcpy(W.win_lo, lo.data(), G * 4, cudaMemcpyHostToDevice));
     int wmax = 0;
     for (int c = 0; c < G; ++c) wmax = std::max(wmax, hi[c] - lo[c]);
     // ---- chunk tables for the staged kernel
@@ -2040,13 +2256,20 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
   W.accx32 = dalloc<float>(h, n);
   W.g64 = dalloc<double>(h, P.k + P.me + 1);
   W.coefA = dalloc<double>(h, P.m + 1);
+  W.dinv = dalloc<double>(h, nkp);
+  if (W.rows_ok) {
+    W.p32_0 = dalloc<float>(h, nkp);
+    W.p32_1 = dalloc<float>(h, nkp);
+    W.y32 = dalloc<float>(h, nkp);
+    if (!W.p32_0 || !W.p32_1 || !W.y32) return kq_fail(h, KQ_ERR_OOM, "pcg FP32 copies");
+  }
   W.slots = dalloc<double>(h, 4 * G);
   W.bar = dalloc<unsigned int>(h, 2);
   W.err = dalloc<int>(h, 1);
   W.iters = dalloc<int>(h, 1);
   W.resn = dalloc<double>(h, 2);
   if (!W.r || !W.y || !W.pb0 || !W.pb1 || !W.qlam || !W.accx64 || !W.accx32 || !W.g64 ||
-      !W.slots || !W.bar || !W.err || !W.iters || !W.resn || !W.coefA)
+      !W.slots || !W.bar || !W.err || !W.iters || !W.resn || !W.coefA || !W.dinv)
     return kq_fail(h, KQ_ERR_OOM, "pcg work space");
   KQ_CUDA(h, cudaMemset(W.accx64, 0, n * sizeof(double)));
   KQ_CUDA(h, cudaMemset(W.accx32, 0, n * sizeof(float)));
@@ -2093,7 +2316,11 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
     rc = launch(h, prec, res, dz, rel, budget, 0, &it, nullptr, nullptr);
     s.kernel_ms += g_last_ms;
     total += it;
-    if (prec == KQ_PREC_F64) s.iters_f64 += it;
+    if (prec == KQ_PREC_F64) {
+      s.iters_f64 += it;
+      s.products_f64 += it;
+      s.kernel_ms_f64 += g_last_ms;
+    }
     s.passes++;
     if (rc != KQ_OK) break;
     k_add<<<256, 256, 0, h->stream>>>(N, z, dz);
@@ -2101,6 +2328,8 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
     float ms = 0.f;
     rc = pcg_apply(h, z, dz, KQ_PREC_F64, &ms);
     s.kernel_ms += ms;
+    s.kernel_ms_f64 += ms;
+    s.products_f64 += 1;
     if (rc != KQ_OK) break;
     const int nb = 256;
     k_axpy_res<<<nb, 256, 0, h->stream>>>(N, rhs, dz, res, h->red);
