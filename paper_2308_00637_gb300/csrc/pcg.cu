@@ -347,6 +347,39 @@ __device__ __forceinline__ T row_dot(const S *r, const T *pw, int64_t n, bool ve
   return warp_sum(dot);
 }
 
+// dots of two rows with the p window (the second row optional): both rows'
+// loads are in flight together
+template <class S, class T>
+__device__ __forceinline__ void row_dot2(const S *r0, const S *r1, bool two, const T *pw, int64_t n,
+                                         bool vec, int lane, T &d0, T &d1) {
+  d0 = (T)0;
+  d1 = (T)0;
+  if (vec) {
+#pragma unroll 2
+    for (int64_t j = 8 * lane; j < n; j += 256) {
+      T v0[8], v1[8];
+      Load8<S, T>::run(r0 + j, v0);
+      if (two) Load8<S, T>::run(r1 + j, v1);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) d0 += v0[k] * pw[j + k];
+      if (two) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k) d1 += v1[k] * pw[j + k];
+      }
+    }
+  } else {
+    for (int64_t j = lane; j < n; j += 32) {
+      d0 += (T)ld_as_f64(r0, j) * pw[j];
+      if (two) d1 += (T)ld_as_f64(r1, j) * pw[j];
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    d0 += __shfl_xor_sync(0xffffffffu, d0, o);
+    d1 += __shfl_xor_sync(0xffffffffu, d1, o);
+  }
+}
+
 template <class HS, class AS>
 struct OpDense {
   // vcta / vG: this CTA's rank and the number of CTAs working on the problem
@@ -378,64 +411,82 @@ struct OpDense {
       acc[j] = (T)0;
     }
     __syncthreads();
-    const int64_t R = n + m + me;
     const int64_t gw0 = (int64_t)vcta * nw + warp, GW = (int64_t)vG * nw;
     const int64_t lo_off = n + me, up_off = n + me + m;
-    for (int64_t row = gw0; row < R; row += GW) {
-      if (row < n) {
-        const T dot = row_dot<HS, T>(Hd + row * hld, pw, n, hvec, lane) * (T)P.hscale;
+    // H rows, two per warp step
+    for (int64_t row = gw0; row < n; row += 2 * GW) {
+      const int64_t r2 = row + GW;
+      const bool two = r2 < n;
+      T d0, d1;
+      row_dot2<HS, T>(Hd + row * hld, Hd + (two ? r2 : row) * hld, two, pw, n, hvec, lane, d0, d1);
+      if (lane == 0) {
+        d0 *= (T)P.hscale;
+        atomicAdd(acc + row, d0);
+        pq += (ldcg(ysrc + row) + beta * ldcg(pold + row)) * (double)d0;
+        if (two) {
+          d1 *= (T)P.hscale;
+          atomicAdd(acc + r2, d1);
+          pq += (ldcg(ysrc + r2) + beta * ldcg(pold + r2)) * (double)d1;
+        }
+      }
+    }
+    // A rows, two per warp step: t = rho A_i p, coefficient, bottom entries
+    auto arow = [&](int64_t ai, T dot) {
+      const bool hl = P.hasl[ai] != 0, hu = P.hasu[ai] != 0;
+      if (!hl && !hu) {
         if (lane == 0) {
-          atomicAdd(acc + row, dot);
-          const double prow = ldcg(ysrc + row) + beta * ldcg(pold + row);
-          pq += prow * (double)dot;
+          a.qlam[me + ai] = 0.0;
+          a.qlam[me + m + ai] = 0.0;
+          if (colpass) a.coefA[ai] = 0.0;
         }
-      } else if (row < n + m) {
-        const int64_t ai = row - n;
-        const bool hl = P.hasl[ai] != 0, hu = P.hasu[ai] != 0;
-        if (!hl && !hu) {
-          if (lane == 0) {
-            a.qlam[me + ai] = 0.0;
-            a.qlam[me + m + ai] = 0.0;
-            if (colpass) a.coefA[ai] = 0.0;
-          }
-          continue;
-        }
-        const AS *ar = Ad + ai * ald;
-        const T dot = row_dot<AS, T>(ar, pw, n, avec, lane);
-        const double rho_a = P.rhoA[ai];
-        const double t = rho_a * (double)dot;
-        const double pl = hl ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
-        const double pu = hu ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
-        const double coef = 2.0 * t * (a.cl[ai] + a.cu[ai]) + pl - pu;
-        if (colpass) {
-          if (lane == 0) a.coefA[ai] = coef * rho_a;
-        } else {
-          const T cf = (T)(coef * rho_a);
-          for (int64_t j = lane; j < n; j += 32) atomicAdd(acc + j, cf * (T)ld_as_f64(ar, j));
-        }
-        if (lane == 0) {
-          const double ql = hl ? t + a.Dl[ai] * pl : 0.0;
-          const double qu = hu ? -t + a.Du[ai] * pu : 0.0;
-          a.qlam[me + ai] = ql;
-          a.qlam[me + m + ai] = qu;
-          pq += coef * t + pl * ql + pu * qu;
-        }
+        return;
+      }
+      const double rho_a = P.rhoA[ai];
+      const double t = rho_a * (double)dot;
+      const double pl = hl ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
+      const double pu = hu ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
+      const double coef = 2.0 * t * (a.cl[ai] + a.cu[ai]) + pl - pu;
+      if (colpass) {
+        if (lane == 0) a.coefA[ai] = coef * rho_a;
       } else {
-        const int64_t e = row - n - m;
-        const double *cr = P.Cd + e * n;
-        T dot = (T)0;
-        for (int64_t j = lane; j < n; j += 32) dot += (T)cr[j] * pw[j];
-        dot = warp_sum(dot);
-        const double t = (double)dot;
-        const double pe = ldcg(ysrc + n + e) + beta * ldcg(pold + n + e);
-        const double coef = 2.0 * t / a.mu + pe;
-        const T cf = (T)coef;
-        for (int64_t j = lane; j < n; j += 32) atomicAdd(acc + j, cf * (T)cr[j]);
-        if (lane == 0) {
-          const double qe = t + a.mu * pe;
-          a.qlam[e] = qe;
-          pq += coef * t + pe * qe;
-        }
+        const T cf = (T)(coef * rho_a);
+        const AS *ar = Ad + ai * ald;
+        for (int64_t j = lane; j < n; j += 32) atomicAdd(acc + j, cf * (T)ld_as_f64(ar, j));
+      }
+      if (lane == 0) {
+        const double ql = hl ? t + a.Dl[ai] * pl : 0.0;
+        const double qu = hu ? -t + a.Du[ai] * pu : 0.0;
+        a.qlam[me + ai] = ql;
+        a.qlam[me + m + ai] = qu;
+        pq += coef * t + pl * ql + pu * qu;
+      }
+    };
+    // warps continue the global row numbering after the H rows
+    const int64_t a0 = ((gw0 - n) % GW + GW) % GW;   // first A row of this warp
+    for (int64_t ai = a0; ai < m; ai += 2 * GW) {
+      const int64_t a2 = ai + GW;
+      const bool two = a2 < m;
+      T d0, d1;
+      row_dot2<AS, T>(Ad + ai * ald, Ad + (two ? a2 : ai) * ald, two, pw, n, avec, lane, d0, d1);
+      arow(ai, d0);
+      if (two) arow(a2, d1);
+    }
+    // equality rows
+    const int64_t e0 = ((gw0 - n - m) % GW + GW) % GW;
+    for (int64_t e = e0; e < me; e += GW) {
+      const double *cr = P.Cd + e * n;
+      T dot = (T)0;
+      for (int64_t j = lane; j < n; j += 32) dot += (T)cr[j] * pw[j];
+      dot = warp_sum(dot);
+      const double t = (double)dot;
+      const double pe = ldcg(ysrc + n + e) + beta * ldcg(pold + n + e);
+      const double coef = 2.0 * t / a.mu + pe;
+      const T cf = (T)coef;
+      for (int64_t j = lane; j < n; j += 32) atomicAdd(acc + j, cf * (T)cr[j]);
+      if (lane == 0) {
+        const double qe = t + a.mu * pe;
+        a.qlam[e] = qe;
+        pq += coef * t + pe * qe;
       }
     }
     __syncthreads();
@@ -999,6 +1050,7 @@ __host__ __device__ inline RowsLayout rows_layout(int rws, int nw, int a_cap) {
   return L;
 }
 
+// L2 bulk prefetch; the caller passes a 16-byte aligned address
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   if (bytes >= 16)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes & ~15u) : "memory");
@@ -1024,8 +1076,14 @@ struct OpCsrRows {
     const int *st = pf_state();
     const int b = st[0] + step * st[2], e = min(st[1], b + st[2]);
     if (b >= e) return;
+    // values: float4 groups, 16-byte aligned
     prefetch_l2(a.rval4 + b, (uint32_t)(e - b) * 16u);
-    prefetch_l2(a.rcol2 + b, (uint32_t)(e - b) * 8u);
+    // columns: 8 bytes per group; the bulk prefetch needs a 16-byte aligned
+    // start and size, so the byte range is rounded out to 16-byte boundaries
+    // (the column array ends with one spare group, so the end stays inside it)
+    const uint64_t cb = ((uint64_t)b * 8u) & ~(uint64_t)15;
+    const uint64_t ce = ((uint64_t)e * 8u + 15u) & ~(uint64_t)15;
+    prefetch_l2(reinterpret_cast<const unsigned char *>(a.rcol2) + cb, (uint32_t)(ce - cb));
   }
 
   template <class T>
