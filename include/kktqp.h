@@ -97,7 +97,9 @@ typedef struct {
   double pcg_tol;          /* relative unpreconditioned residual (1e-7)         */
   int pcg_maxit;           /* PCG iterations per Newton solve (5000)            */
   int precision;           /* KQ_PREC_*                                         */
-  int refine_steps;        /* MIXED: FP32 correction solves before FP64 rescue  */
+  int refine_steps;        /* MIXED: FP32 correction solves before FP64 (6); the */
+                           /* batched solver hands a QP to FP64 earlier once one*/
+                           /* of its FP32 solves fails to halve its residual    */
   double inner_tol;        /* MIXED: relative tolerance of each FP32 solve      */
   double timeout_s;        /* device barrier budget per wait (seconds)         */
   int grid_ctas;           /* 0 = auto; else persistent-kernel grid size        */

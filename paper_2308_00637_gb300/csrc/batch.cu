@@ -51,51 +51,72 @@ kq_status batch_pcg(kq_batch b, const std::vector<int> &act, const kq_pcg_opts &
   }
   const int mixed = o.precision == KQ_PREC_MIXED;
   const int max_passes = (mixed ? o.refine_steps : 0) + 3;
+  // per QP: FP32 correction passes while they pay (a pass that does not halve
+  // the true residual hands that QP to FP64 passes)
+  std::vector<int> fp32_ok(k, mixed ? 1 : 0);
+  std::vector<double> resn_before(k, 0.0);
   for (int pass = 0; pass < max_passes; ++pass) {
-    const int prec = (mixed && pass < o.refine_steps) ? KQ_PREC_MIXED : KQ_PREC_F64;
     std::vector<int> idx;
-    std::vector<const double *> rhs;
-    std::vector<double *> out;
-    std::vector<double> tol;
-    std::vector<int> maxit;
     std::vector<int> map;
-    std::vector<double> wts;
+    std::vector<int> pprec;
     for (int j = 0; j < k; ++j) {
       if (done[j]) continue;
       const int budget = o.maxit - used[j];
       if (budget <= 0) { done[j] = 1; continue; }
-      kq_problem *h = hs[act[j]];
-      double rel = pass == 0 ? o.tol : o.tol * bnorm[j] / std::max(resn[j], 1e-300);
-      if (prec == KQ_PREC_MIXED) rel = std::max(rel, o.inner_tol);
-      rel = std::min(rel, 0.5);
       idx.push_back(act[j]);
-      rhs.push_back(h->tmp);
-      out.push_back(h->zref);
-      tol.push_back(rel);
-      maxit.push_back(budget);
       map.push_back(j);
-      wts.push_back(last_iters[act[j]]);
+      pprec.push_back((fp32_ok[j] && pass < o.refine_steps) ? KQ_PREC_MIXED : KQ_PREC_F64);
+      resn_before[j] = resn[j];
     }
     if (idx.empty()) break;
+    // one launch per precision group
+    for (int prec : {KQ_PREC_MIXED, KQ_PREC_F64}) {
+      std::vector<int> gidx, gmap;
+      std::vector<const double *> rhs;
+      std::vector<double *> out;
+      std::vector<double> tol, wts;
+      std::vector<int> maxit;
+      for (size_t q = 0; q < idx.size(); ++q) {
+        if (pprec[q] != prec) continue;
+        const int j = map[q];
+        kq_problem *h = hs[act[j]];
+        double rel = pass == 0 ? o.tol : o.tol * bnorm[j] / std::max(resn[j], 1e-300);
+        if (prec == KQ_PREC_MIXED) rel = std::max(rel, o.inner_tol);
+        rel = std::min(rel, 0.5);
+        gidx.push_back(act[j]);
+        gmap.push_back(j);
+        rhs.push_back(h->tmp);
+        out.push_back(h->zref);
+        tol.push_back(rel);
+        maxit.push_back(o.maxit - used[j]);
+        wts.push_back(last_iters[act[j]]);
+      }
+      if (gidx.empty()) continue;
+      std::vector<int> its, errs;
+      std::vector<double> rr, bb;
+      float ms = 0.f;
+      std::string e;
+      kq_status rc = batch_pcg_launch(b->B, hs, gidx, rhs, out, tol, maxit, 0, prec, s, its, errs,
+                                      rr, bb, &ms, e, &wts);
+      if (rc != KQ_OK) return bfail(b, rc, e);
+      *kernel_ms += ms;
+      for (size_t q = 0; q < gidx.size(); ++q) {
+        const int j = gmap[q];
+        if (errs[q] != 0)
+          return bfail(b, errs[q] == 7 ? KQ_ERR_TIMEOUT : (errs[q] == 4 ? KQ_ERR_NOT_CONVEX : KQ_ERR_NUMERIC),
+                       "batched PCG failed on QP " + std::to_string(act[j]));
+        if (pass == 0) bnorm[j] = std::sqrt(bb[q]);
+        used[j] += its[q];
+        iters_out[j] += its[q];
+        kq_problem *h = hs[act[j]];
+        vec_add_enqueue(h, h->z, h->zref);
+      }
+    }
     std::vector<int> its, errs;
     std::vector<double> rr, bb;
     float ms = 0.f;
     std::string e;
-    kq_status rc = batch_pcg_launch(b->B, hs, idx, rhs, out, tol, maxit, 0, prec, s, its, errs, rr,
-                                    bb, &ms, e, &wts);
-    if (rc != KQ_OK) return bfail(b, rc, e);
-    *kernel_ms += ms;
-    for (size_t q = 0; q < idx.size(); ++q) {
-      const int j = map[q];
-      if (errs[q] != 0)
-        return bfail(b, errs[q] == 7 ? KQ_ERR_TIMEOUT : (errs[q] == 4 ? KQ_ERR_NOT_CONVEX : KQ_ERR_NUMERIC),
-                     "batched PCG failed on QP " + std::to_string(act[j]));
-      if (pass == 0) bnorm[j] = std::sqrt(bb[q]);
-      used[j] += its[q];
-      iters_out[j] += its[q];
-      kq_problem *h = hs[act[j]];
-      vec_add_enqueue(h, h->z, h->zref);
-    }
+    kq_status rc;
     // FP64 K z for every QP of this pass in one launch, then res = rhs - K z
     std::vector<const double *> zin;
     std::vector<double *> kz;
@@ -119,6 +140,8 @@ kq_status batch_pcg(kq_batch b, const std::vector<int> &act, const kq_pcg_opts &
       const int j = map[q];
       resn[j] = std::sqrt(hs[idx[q]]->h_red[8]);
       if (!(resn[j] == resn[j])) return bfail(b, KQ_ERR_NUMERIC, "batched PCG residual NaN");
+      if (pprec[q] == KQ_PREC_MIXED && pass > 0 && resn[j] > 0.5 * resn_before[j]) fp32_ok[j] = 0;
+      if (pprec[q] == KQ_PREC_MIXED && pass == 0 && resn[j] > 0.5 * bnorm[j]) fp32_ok[j] = 0;
       if (resn[j] <= o.tol * bnorm[j] || bnorm[j] == 0.0) done[j] = 1;
       else if (used[j] >= o.maxit) { done[j] = 1; maxit_hit[j] = 1; }
     }

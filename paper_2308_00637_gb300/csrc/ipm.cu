@@ -770,7 +770,7 @@ void kq_default_ipm_opts(kq_ipm_opts *o) {
   o->pcg_tol = 1e-7;
   o->pcg_maxit = 5000;
   o->precision = KQ_PREC_F64;
-  o->refine_steps = 2;
+  o->refine_steps = 6;
   o->inner_tol = 1e-4;
   o->timeout_s = 2.0;
   o->grid_ctas = 0;
@@ -782,7 +782,7 @@ void kq_default_pcg_opts(kq_pcg_opts *o) {
   o->tol = 1e-7;
   o->maxit = 5000;
   o->precision = KQ_PREC_F64;
-  o->refine_steps = 2;
+  o->refine_steps = 6;
   o->inner_tol = 1e-4;
 }
 

@@ -2363,6 +2363,8 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
   const int mixed = o.precision == KQ_PREC_MIXED;
   const int max_passes = (mixed ? o.refine_steps : 0) + 3;
   kq_status rc = KQ_OK;
+  // up to refine_steps FP32 correction passes, each restarted from the true
+  // (FP64) residual, then FP64 passes
   for (int pass = 0; pass < max_passes; ++pass) {
     const int prec = (mixed && pass < o.refine_steps) ? KQ_PREC_MIXED : KQ_PREC_F64;
     double rel = o.tol * bn / resn;
