@@ -229,7 +229,7 @@ def run_other(args):
                  "objective": qp.objective(x), "n": qp.n}
             if args.workload == "c4":
                 gbar = qpgen.config4_directions(qp, 1)[0]
-                po = kq.default_pcg_opts(tol=1e-7)
+                po = kq.default_pcg_opts(tol=1e-7, precision=prec)
                 tb = []
                 for k in range(warm + steps):
                     torch.cuda.synchronize()
@@ -378,20 +378,25 @@ def main():
     if prec == kq.KQ_PREC_MIXED:
         prod_dom = prod - sum(s.pcg_products_f64 for s in stats)
         kms_dom = kms - sum(s.pcg_kernel_ms_f64 for s in stats)
+        launches_dom = launches - sum(s.pcg_launches_f64 for s in stats)
         kname = "pcg_kernel<OpCsrRows, float> (persistent FP32 PCG pass)"
     else:
-        prod_dom, kms_dom = prod, kms
+        prod_dom, kms_dom, launches_dom = prod, kms, launches
         kname = "pcg_kernel<OpCsrStaged, double> (persistent FP64 PCG solve)"
     abytes = algo_bytes(qp)
     achieved = prod_dom * abytes / (kms_dom * 1e-3) / 1e9
     peak, peak_src = read_peaks()
-    traffic = None
+    # DRAM bytes of the dominant kernel from the committed ncu capture (null once
+    # the kernel source has changed since): per K*v product, and per launch of
+    # this run (products per launch of the timed region)
+    traffic = traffic_pp = None
     try:
         tr = json.load(open(TRAFFIC_FILE))
         if tr.get("kernel_hash") == kernel_source_hash() and tr.get("precision") == args.precision:
-            traffic = tr["dram_bytes_per_launch_product"] * (prod / max(1, launches))
+            traffic_pp = tr["dram_bytes_per_product"]
+            traffic = traffic_pp * (prod_dom / max(1, launches_dom))
     except Exception:
-        traffic = None
+        traffic = traffic_pp = None
     # accuracy of the result (original units), checked by the CPU oracle's metric code
     x = dev["x"].cpu().numpy()
     out = {k: v.cpu().numpy() for k, v in dev.items()}
@@ -473,8 +478,11 @@ def main():
                          "frac": achieved / peak, "traffic": traffic,
                          "peak_source": peak_src,
                          "kernel": kname, "products": int(prod_dom),
+                         "launches": int(launches_dom), "traffic_per_product": traffic_pp,
                          "kernel_ms": kms_dom,
-                         "algorithmic_bytes_per_product": abytes, "note": ALGO_BYTES_NOTE,
+                         "algorithmic_bytes_per_product": abytes,
+                         "algorithmic_bytes_per_launch": abytes * prod_dom / max(1, launches_dom),
+                         "note": ALGO_BYTES_NOTE,
                          "stored_bytes_per_product": stored_bytes(qp) if prec == kq.KQ_PREC_MIXED
                          else abytes},
             "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": h2d,

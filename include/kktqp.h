@@ -123,6 +123,7 @@ typedef struct {
   long long pcg_iters_f64; /* MIXED: PCG iterations run in FP64 (rescue passes) */
   long long pcg_products_f64;  /* products inside FP64 launches (passes + residuals) */
   double pcg_kernel_ms_f64;    /* device time of the FP64 persistent launches       */
+  long long pcg_launches_f64;  /* FP64 persistent launches (passes + residuals)     */
 } kq_ipm_stats;
 
 typedef struct {
@@ -142,6 +143,7 @@ typedef struct {
   int iters_f64;           /* iterations of FP64 passes (all of them in F64)    */
   int products_f64;        /* products inside FP64 launches (passes + residuals)*/
   double kernel_ms_f64;    /* device time of the FP64 persistent launches       */
+  int launches_f64;        /* FP64 persistent launches (passes + residuals)     */
 } kq_pcg_stats;
 
 /* Fill *o with the paper's settings (gamma 0.99, mu/10, mu_tol 1e-6, PCG tol

@@ -59,7 +59,7 @@ class KqIpmStats(C.Structure):
                 ("pcg_kernel_ms", C.c_double), ("pcg_launches", C.c_longlong),
                 ("pcg_products", C.c_longlong), ("kernel_launches", C.c_longlong),
                 ("pcg_iters_f64", C.c_longlong), ("pcg_products_f64", C.c_longlong),
-                ("pcg_kernel_ms_f64", C.c_double)]
+                ("pcg_kernel_ms_f64", C.c_double), ("pcg_launches_f64", C.c_longlong)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -73,7 +73,8 @@ class KqPcgOpts(C.Structure):
 class KqPcgStats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("passes", C.c_int),
                 ("rel_res", C.c_double), ("kernel_ms", C.c_double), ("iters_f64", C.c_int),
-                ("products_f64", C.c_int), ("kernel_ms_f64", C.c_double)]
+                ("products_f64", C.c_int), ("kernel_ms_f64", C.c_double),
+                ("launches_f64", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -1177,6 +1177,7 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
     st.pcg_iters_f64 += ps.iters_f64;
     st.pcg_products_f64 += ps.products_f64;
     st.pcg_kernel_ms_f64 += ps.kernel_ms_f64;
+    st.pcg_launches_f64 += ps.launches_f64;
     if (rc == KQ_WARN_PCG_MAXIT) st.pcg_maxit_hits++;
     else if (rc != KQ_OK) { final = rc; break; }
     // step recovery (A dx) and ratio test

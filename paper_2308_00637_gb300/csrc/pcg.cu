@@ -2380,6 +2380,7 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
       s.iters_f64 += it;
       s.products_f64 += it;
       s.kernel_ms_f64 += g_last_ms;
+      s.launches_f64 += 1;
     }
     s.passes++;
     if (rc != KQ_OK) break;
@@ -2390,6 +2391,7 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
     s.kernel_ms += ms;
     s.kernel_ms_f64 += ms;
     s.products_f64 += 1;
+    s.launches_f64 += 1;
     if (rc != KQ_OK) break;
     const int nb = 256;
     k_axpy_res<<<nb, 256, 0, h->stream>>>(N, rhs, dz, res, h->red);
