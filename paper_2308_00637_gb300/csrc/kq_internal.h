@@ -145,6 +145,10 @@ struct PcgWork {
   int rws = 0;                 // stride of the per-warp accumulators (floats)
   int pf_dist = 0;             // L2 prefetch distance in warp steps (0: off)
   size_t smem_rows = 0;
+  float *rw2lo = nullptr;      // nP: low part of the FP32-split row weight (FP64 products)
+  bool rows64_ok = false;      // FP64 products also register-streamed
+  size_t smem_rows64 = 0;
+  int threads_rows64 = 256;
   int64_t *row_begin = nullptr;   // G+1 partition of rows (P rows / dense rows)
   int32_t *win_lo = nullptr, *win_hi = nullptr;  // G column windows (CSR)
   int *h_pinned = nullptr;     // pinned host mirror for status words

@@ -62,6 +62,7 @@ struct PcgArgs {
   const RowSlot *rslot;
   const float4 *rval4;
   const uint2 *rcol2;           // four 16-bit window-relative columns per lane
+  const float *rw2lo;           // per P row: 2 sigma w - (float)(2 sigma w) (FP64 products)
   int rws;                      // per-warp accumulator stride (floats, multiple of 32)
   int pf_dist;                  // L2 prefetch distance in warp steps (0: off, the default)
   double *dinv;                 // 1 / diag(K), formed at the start of a solve (or null)
@@ -1034,17 +1035,18 @@ struct OpCsrStaged {
 // Shared memory of the register-streamed operator: the p window, one private
 // accumulator per warp (no atomics in the scatter), the dose-limit constants.
 struct RowsLayout { size_t pw, acc, arho, acs, aDl, aDu, apl, apu, afl, total; };
-__host__ __device__ inline RowsLayout rows_layout(int rws, int nw, int a_cap) {
+// es = size of the product type (4: FP32 products, 8: FP64 products)
+__host__ __device__ inline RowsLayout rows_layout(int rws, int nw, int a_cap, int es) {
   RowsLayout L;
   size_t o = 0;
-  L.pw = o; o += 4 * (size_t)rws;
-  L.acc = o; o += 4 * (size_t)rws * nw;
-  L.arho = o; o += 4 * (size_t)a_cap;
-  L.acs = o; o += 4 * (size_t)a_cap;
-  L.aDl = o; o += 4 * (size_t)a_cap;
-  L.aDu = o; o += 4 * (size_t)a_cap;
-  L.apl = o; o += 4 * (size_t)a_cap;
-  L.apu = o; o += 4 * (size_t)a_cap;
+  L.pw = o; o += es * (size_t)rws;
+  L.acc = o; o += es * (size_t)rws * nw;
+  L.arho = o; o += es * (size_t)a_cap;
+  L.acs = o; o += es * (size_t)a_cap;
+  L.aDl = o; o += es * (size_t)a_cap;
+  L.aDu = o; o += es * (size_t)a_cap;
+  L.apl = o; o += es * (size_t)a_cap;
+  L.apu = o; o += es * (size_t)a_cap;
   L.afl = o; o += (size_t)a_cap;
   L.total = kq_up128(o);
   return L;
@@ -1089,21 +1091,21 @@ struct OpCsrRows {
   template <class T>
   static __device__ void begin(const PcgArgs &a, unsigned char *smem) {
     const int cta = blockIdx.x, tid = threadIdx.x, nw = blockDim.x >> 5;
-    const RowsLayout L = rows_layout(a.rws, nw, a.a_cap);
-    float *acc = reinterpret_cast<float *>(smem + L.acc);
-    for (int j = tid; j < a.rws * nw; j += blockDim.x) acc[j] = 0.f;
+    const RowsLayout L = rows_layout(a.rws, nw, a.a_cap, (int)sizeof(T));
+    T *acc = reinterpret_cast<T *>(smem + L.acc);
+    for (int j = tid; j < a.rws * nw; j += blockDim.x) acc[j] = (T)0;
     const int alo = a.a_lo[cta], na = min(a.a_hi[cta] - alo, a.a_cap);
-    float *arho = reinterpret_cast<float *>(smem + L.arho);
-    float *acs = reinterpret_cast<float *>(smem + L.acs);
-    float *aDl = reinterpret_cast<float *>(smem + L.aDl);
-    float *aDu = reinterpret_cast<float *>(smem + L.aDu);
+    T *arho = reinterpret_cast<T *>(smem + L.arho);
+    T *acs = reinterpret_cast<T *>(smem + L.acs);
+    T *aDl = reinterpret_cast<T *>(smem + L.aDl);
+    T *aDu = reinterpret_cast<T *>(smem + L.aDu);
     uint8_t *afl = smem + L.afl;
     for (int i = tid; i < na; i += blockDim.x) {
       const int ai = alo + i;
-      arho[i] = (float)a.P.rhoA[ai];
-      acs[i] = (float)(a.cl[ai] + a.cu[ai]);
-      aDl[i] = (float)a.Dl[ai];
-      aDu[i] = (float)a.Du[ai];
+      arho[i] = (T)a.P.rhoA[ai];
+      acs[i] = (T)(a.cl[ai] + a.cu[ai]);
+      aDl[i] = (T)a.Dl[ai];
+      aDu[i] = (T)a.Du[ai];
       afl[i] = (uint8_t)((a.P.hasl[ai] ? 1 : 0) | (a.P.hasu[ai] ? 2 : 0));
     }
     if (tid == 0) {
@@ -1125,14 +1127,15 @@ struct OpCsrRows {
   }
 
   // one row's scatter into the warp's accumulator (columns distinct)
-  static __device__ __forceinline__ void scatter(float *accw, const float4 &v, const int4 &c,
-                                                 float u, bool act) {
+  template <class T>
+  static __device__ __forceinline__ void scatter(T *accw, const float4 &v, const int4 &c, T u,
+                                                 bool act) {
     if (act) {
-      const float a0 = accw[c.x], a1 = accw[c.y], a2 = accw[c.z], a3 = accw[c.w];
-      accw[c.x] = fmaf(u, v.x, a0);
-      accw[c.y] = fmaf(u, v.y, a1);
-      accw[c.z] = fmaf(u, v.z, a2);
-      accw[c.w] = fmaf(u, v.w, a3);
+      const T a0 = accw[c.x], a1 = accw[c.y], a2 = accw[c.z], a3 = accw[c.w];
+      accw[c.x] = a0 + u * (T)v.x;
+      accw[c.y] = a1 + u * (T)v.y;
+      accw[c.z] = a2 + u * (T)v.z;
+      accw[c.w] = a3 + u * (T)v.w;
     }
     __syncwarp();
   }
@@ -1141,23 +1144,22 @@ struct OpCsrRows {
   static __device__ double phaseA(const PcgArgs &a, const double *ysrc, const double *pold,
                                   double *pnew, double beta, int64_t vb, int64_t ve,
                                   unsigned char *smem, bool &ok) {
-    static_assert(sizeof(T) == 4, "register-streamed CSR runs FP32 products");
     const DevProb &P = a.P;
     const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nw = blockDim.x >> 5;
-    const RowsLayout L = rows_layout(a.rws, nw, a.a_cap);
+    const RowsLayout L = rows_layout(a.rws, nw, a.a_cap, (int)sizeof(T));
     const int lo = a.win_lo[cta], wlen = a.win_hi[cta] - lo;
-    float *pw = reinterpret_cast<float *>(smem + L.pw);
-    float *acc = reinterpret_cast<float *>(smem + L.acc);
-    float *accw = acc + (size_t)warp * a.rws;
-    float *accg = reinterpret_cast<float *>(a.accx);
+    T *pw = reinterpret_cast<T *>(smem + L.pw);
+    T *acc = reinterpret_cast<T *>(smem + L.acc);
+    T *accw = acc + (size_t)warp * a.rws;
+    T *accg = reinterpret_cast<T *>(a.accx);
     const int alo = a.a_lo[cta], na = min(a.a_hi[cta] - alo, a.a_cap);
-    const float *arho = reinterpret_cast<const float *>(smem + L.arho);
-    const float *acs = reinterpret_cast<const float *>(smem + L.acs);
-    const float *aDl = reinterpret_cast<const float *>(smem + L.aDl);
-    const float *aDu = reinterpret_cast<const float *>(smem + L.aDu);
-    float *apl = reinterpret_cast<float *>(smem + L.apl);
-    float *apu = reinterpret_cast<float *>(smem + L.apu);
+    const T *arho = reinterpret_cast<const T *>(smem + L.arho);
+    const T *acs = reinterpret_cast<const T *>(smem + L.acs);
+    const T *aDl = reinterpret_cast<const T *>(smem + L.aDl);
+    const T *aDu = reinterpret_cast<const T *>(smem + L.aDu);
+    T *apl = reinterpret_cast<T *>(smem + L.apl);
+    T *apu = reinterpret_cast<T *>(smem + L.apu);
     const uint8_t *afl = smem + L.afl;
     const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
     const int64_t r0 = a.row_begin[cta];
@@ -1181,7 +1183,7 @@ struct OpCsrRows {
       if (lane < x0.len4) { v0 = __ldcs(a.rval4 + x0.off4 + lane); c0 = __ldcs(a.rcol2 + x0.off4 + lane); }
       if (lane < x1.len4) { v1 = __ldcs(a.rval4 + x1.off4 + lane); c1 = __ldcs(a.rcol2 + x1.off4 + lane); }
     };
-    float pqt = 0.f;
+    T pqt = (T)0;
     // one pair of rows: dots with the window, coefficients, scatter
     auto process = [&](int ii, const RowSlot &s0, const RowSlot &s1, const float4 &v0,
                        const float4 &v1, const uint2 &p0, const uint2 &p1) {
@@ -1191,24 +1193,32 @@ struct OpCsrRows {
                                 (int)(p1.y >> 16));
       const bool has1 = ii + 1 < nr;
       const bool act0 = lane < s0.len4, act1 = lane < s1.len4;
-      float d0 = 0.f, d1 = 0.f;
-      if (act0) d0 = v0.x * pw[c0.x] + v0.y * pw[c0.y] + v0.z * pw[c0.z] + v0.w * pw[c0.w];
-      if (act1) d1 = v1.x * pw[c1.x] + v1.y * pw[c1.y] + v1.z * pw[c1.z] + v1.w * pw[c1.w];
+      // FP64 products: the low part of the FP32-split row weight
+      float w0lo = 0.f, w1lo = 0.f;
+      if constexpr (sizeof(T) == 8) {
+        w0lo = __ldg(a.rw2lo + r0 + ii);
+        if (has1) w1lo = __ldg(a.rw2lo + r0 + ii + 1);
+      }
+      T d0 = (T)0, d1 = (T)0;
+      if (act0)
+        d0 = (T)v0.x * pw[c0.x] + (T)v0.y * pw[c0.y] + (T)v0.z * pw[c0.z] + (T)v0.w * pw[c0.w];
+      if (act1)
+        d1 = (T)v1.x * pw[c1.x] + (T)v1.y * pw[c1.y] + (T)v1.z * pw[c1.z] + (T)v1.w * pw[c1.w];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         d0 += __shfl_xor_sync(0xffffffffu, d0, o);
         d1 += __shfl_xor_sync(0xffffffffu, d1, o);
       }
-      const RowDesc rd0{0, s0.a, s0.w2, 0.f}, rd1{0, s1.a, s1.w2, 0.f};
-      const float u0 = OpCsrStaged::row_coef<float>(a, rd0, d0, ysrc, pold, beta, alo, na, arho,
-                                                    acs, aDl, aDu, apl, apu, afl, lane, pqt);
-      float u1 = 0.f;
+      const RowDesc rd0{0, s0.a, s0.w2, w0lo}, rd1{0, s1.a, s1.w2, w1lo};
+      const T u0 = OpCsrStaged::row_coef<T>(a, rd0, d0, ysrc, pold, beta, alo, na, arho, acs, aDl,
+                                            aDu, apl, apu, afl, lane, pqt);
+      T u1 = (T)0;
       if (has1)
-        u1 = OpCsrStaged::row_coef<float>(a, rd1, d1, ysrc, pold, beta, alo, na, arho, acs, aDl,
-                                          aDu, apl, apu, afl, lane, pqt);
+        u1 = OpCsrStaged::row_coef<T>(a, rd1, d1, ysrc, pold, beta, alo, na, arho, acs, aDl, aDu,
+                                      apl, apu, afl, lane, pqt);
       if (lane == 0) pqt += u0 * d0 + u1 * d1;
-      scatter(accw, v0, c0, u0, act0);
-      scatter(accw, v1, c1, u1, act1);
+      scatter<T>(accw, v0, c0, u0, act0);
+      scatter<T>(accw, v1, c1, u1, act1);
     };
     int i = 2 * warp;
     const int stp = 2 * nw;
@@ -1221,7 +1231,7 @@ struct OpCsrRows {
     double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
     ld_data(sa0, sa1, va0, va1, ca0, ca1);
     ld_data(sb0, sb1, vb0, vb1, cb0, cb1);
-    const float *p32o = a.apply ? nullptr : p32_of(a, pold);
+    const float *p32o = (a.apply || sizeof(T) != 4) ? nullptr : p32_of(a, pold);
     if (p32o && a.y32) {
       // window p from the FP32 copies of y and p_old (FP32 arithmetic: the
       // product rounds p to FP32 anyway)
@@ -1230,23 +1240,23 @@ struct OpCsrRows {
       for (int j = tid; j < wlen + 2 * na; j += blockDim.x) {
         if (j < wlen) {
           const int c = lo + j;
-          pw[j] = fmaf(b32, __ldcg(p32o + c), __ldcg(a.y32 + c));
+          pw[j] = (T)fmaf(b32, __ldcg(p32o + c), __ldcg(a.y32 + c));
         } else {
           const int k = (j - wlen) >> 1, up = (j - wlen) & 1;
           const int64_t ix = (up ? up_off : lo_off) + alo + k;
           const float v = (afl[k] & (up ? 2 : 1)) ? fmaf(b32, __ldcg(p32o + ix), __ldcg(a.y32 + ix)) : 0.f;
-          if (up) apu[k] = v; else apl[k] = v;
+          if (up) apu[k] = (T)v; else apl[k] = (T)v;
         }
       }
     } else {
       for (int j = tid; j < wlen; j += blockDim.x) {
         const int c = lo + j;
-        pw[j] = (float)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+        pw[j] = (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
       }
       for (int k = tid; k < na; k += blockDim.x) {
         const int ai = alo + k;
-        apl[k] = (float)((afl[k] & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0);
-        apu[k] = (float)((afl[k] & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0);
+        apl[k] = (T)((afl[k] & 1) ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0);
+        apu[k] = (T)((afl[k] & 2) ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0);
       }
     }
     __syncthreads();
@@ -1265,7 +1275,24 @@ struct OpCsrRows {
     }
     __syncthreads();
     // sum the private copies into the global accumulator; zero them
-    float4 *acc4 = reinterpret_cast<float4 *>(acc);
+    if constexpr (sizeof(T) == 8) {
+      double2 *acc2 = reinterpret_cast<double2 *>(acc);
+      const int ws2 = a.rws >> 1;
+      for (int j2 = tid; j2 < ws2; j2 += blockDim.x) {
+        double2 t = make_double2(0.0, 0.0);
+        for (int w = 0; w < nw; ++w) {
+          const double2 x = acc2[(size_t)w * ws2 + j2];
+          t.x += x.x; t.y += x.y;
+          acc2[(size_t)w * ws2 + j2] = make_double2(0.0, 0.0);
+        }
+        const int c = 2 * j2;
+        if (c < wlen && t.x != 0.0) atomicAdd(reinterpret_cast<double *>(accg) + lo + c, t.x);
+        if (c + 1 < wlen && t.y != 0.0) atomicAdd(reinterpret_cast<double *>(accg) + lo + c + 1, t.y);
+      }
+      (void)ok;
+      return pq + (double)pqt;
+    }
+    float4 *acc4 = reinterpret_cast<float4 *>(reinterpret_cast<float *>(acc));
     const int ws4 = a.rws >> 2;
     for (int j4 = tid; j4 < ws4; j4 += blockDim.x) {
       float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -1278,12 +1305,13 @@ struct OpCsrRows {
       if (c + 3 < wlen) {
         // lo is a multiple of 4: one 16-byte vector reduction
         if (t.x != 0.f || t.y != 0.f || t.z != 0.f || t.w != 0.f)
-          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(accg + lo + c),
+          asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(reinterpret_cast<float *>(accg) + lo + c),
                        "f"(t.x), "f"(t.y), "f"(t.z), "f"(t.w) : "memory");
       } else {
-        if (c + 0 < wlen && t.x != 0.f) atomicAdd(accg + lo + c + 0, t.x);
-        if (c + 1 < wlen && t.y != 0.f) atomicAdd(accg + lo + c + 1, t.y);
-        if (c + 2 < wlen && t.z != 0.f) atomicAdd(accg + lo + c + 2, t.z);
+        float *ag = reinterpret_cast<float *>(accg);
+        if (c + 0 < wlen && t.x != 0.f) atomicAdd(ag + lo + c + 0, t.x);
+        if (c + 1 < wlen && t.y != 0.f) atomicAdd(ag + lo + c + 1, t.y);
+        if (c + 2 < wlen && t.z != 0.f) atomicAdd(ag + lo + c + 2, t.z);
       }
     }
     // prefetch the first steps of the next product (the matrix does not change)
@@ -1514,6 +1542,16 @@ __global__ void __launch_bounds__(512, 1) pcg_kernel(PcgArgs a) {
   pcg_body<OP, T>(a, blockIdx.x, gridDim.x, smem, sh, sbuf);
 }
 
+// the same with 256 threads (the FP64 register-streamed products: half the
+// warps, each with twice the registers)
+template <class OP, class T>
+__global__ void __launch_bounds__(256, 1) pcg_kernel_256(PcgArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sh[32 * 2];
+  __shared__ double sbuf[512];
+  pcg_body<OP, T>(a, blockIdx.x, gridDim.x, smem, sh, sbuf);
+}
+
 // Batched dense PCG: CTA b belongs to team cta_team[b]; a team works through
 // its list of problems one after another, each with pcg_body on the team's
 // CTAs (team-local bounded barrier in that problem's GridBar).
@@ -1655,11 +1693,17 @@ kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double t
   a.pf_dist = W.pf_dist;
   KFun f = prec == KQ_PREC_MIXED ? pick_kernel<float>(h->P) : pick_kernel<double>(h->P);
   size_t smem = W.smem;
+  int threads = W.threads;
   a.dinv = W.dinv;
+  a.rw2lo = W.rw2lo;
   if (prec == KQ_PREC_MIXED && W.rows_ok) {
     f = pcg_kernel<OpCsrRows, float>;
     smem = W.smem_rows;
     a.p32_0 = W.p32_0; a.p32_1 = W.p32_1; a.y32 = W.y32;
+  } else if (prec == KQ_PREC_F64 && W.rows_ok && W.rows64_ok) {
+    f = pcg_kernel_256<OpCsrRows, double>;
+    smem = W.smem_rows64;
+    threads = W.threads_rows64;
   }
   KQ_CUDA(h, cudaFuncSetAttribute((const void *)f, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)smem));
@@ -1667,7 +1711,7 @@ kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double t
   KQ_CUDA(h, cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), h->stream));
   void *args[] = {&a};
   KQ_CUDA(h, cudaEventRecord(h->ev0, h->stream));
-  KQ_CUDA(h, cudaLaunchCooperativeKernel((const void *)f, dim3(W.G), dim3(W.threads), args,
+  KQ_CUDA(h, cudaLaunchCooperativeKernel((const void *)f, dim3(W.G), dim3(threads), args,
                                          smem, h->stream));
   ++h->launches;
   ++h->pcg_launches;
@@ -2064,8 +2108,10 @@ bool build_rows_layout(kq_problem *h, int G, int threads, const std::vector<int6
   if (wmax > 65536) return false;     // columns are stored as 16-bit window offsets
   const int rws = (wmax + 31) & ~31;
   const int nw = threads / 32;
-  const size_t smem = rows_layout(rws, nw, W.a_cap).total;
+  const size_t smem = rows_layout(rws, nw, W.a_cap, 4).total;
   if (smem > 220 * 1024) return false;
+  // FP64 products: half the warps (their private accumulators are twice as wide)
+  const size_t smem64 = rows_layout(rws, nw / 2, W.a_cap, 8).total;
   std::vector<RowSlot> slots(std::max<int64_t>(nP, 1));
   int64_t tot4 = 0;
   for (int c = 0; c < G; ++c) {
@@ -2097,8 +2143,20 @@ bool build_rows_layout(kq_problem *h, int G, int threads, const std::vector<int6
       cudaMemcpyAsync(&e, d_err, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
       cudaStreamSynchronize(h->stream) != cudaSuccess || e != 0)
     return false;
+  // low parts of the FP32-split row weights (FP64 products)
+  {
+    std::vector<float> lo2(std::max<int64_t>(nP, 1), 0.f);
+    for (int64_t r = 0; r < nP; ++r) lo2[r] = (float)(w2[r] - (double)(float)w2[r]);
+    W.rw2lo = dalloc<float>(h, lo2.size());
+    if (!W.rw2lo ||
+        cudaMemcpy(W.rw2lo, lo2.data(), lo2.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
+      return false;
+  }
   W.rws = rws;
   W.smem_rows = smem;
+  W.rows64_ok = smem64 <= 220 * 1024;
+  W.smem_rows64 = smem64;
+  W.threads_rows64 = threads / 2;
   {
     const char *pf = getenv("KQ_PF");
     W.pf_dist = pf ? std::max(0, atoi(pf)) : 0;
@@ -2303,6 +2361,12 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
       KQ_CUDA(h, cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W.smem_rows));
       KQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fr, threads, W.smem_rows));
       if (per_sm * sms < G) W.rows_ok = false;
+    }
+    if (W.rows_ok && W.rows64_ok) {
+      const void *fr = (const void *)pcg_kernel_256<OpCsrRows, double>;
+      KQ_CUDA(h, cudaFuncSetAttribute(fr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)W.smem_rows64));
+      KQ_CUDA(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fr, W.threads_rows64, W.smem_rows64));
+      if (per_sm * sms < G) W.rows64_ok = false;
     }
   }
   W.r = dalloc<double>(h, nkp);
