@@ -115,6 +115,11 @@ __device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int *p) {
 
 __device__ __forceinline__ bool grid_sync(const GridBar &g) {
   __shared__ int s_ok;
+  if (g.nblocks == 1) {
+    // a single CTA: the CTA barrier orders its global and shared memory
+    __syncthreads();
+    return true;
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;

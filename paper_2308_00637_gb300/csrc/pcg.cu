@@ -1052,6 +1052,24 @@ __host__ __device__ inline RowsLayout rows_layout(int rws, int nw, int a_cap, in
   return L;
 }
 
+// FP32 -> FP64 on the integer pipe (IEEE-754 binary32 -> binary64 re-encoding:
+// sign kept, exponent rebased by 1023 - 127 = 896, mantissa shifted left by
+// 29).  Exact for every normal number and zero; subnormals, infinities and
+// NaN take the hardware conversion.  The SM's FP64 unit is narrow, and the
+// hardware conversion runs on it.
+__device__ __forceinline__ double f32_to_f64(float f) {
+  const uint32_t b = __float_as_uint(f);
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
+  if (e == 0u && (b & 0x7fffffu) == 0u) return __longlong_as_double((long long)sign);
+  if (e == 0u || e == 0xffu) return (double)f;
+  return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) |
+                                          ((uint64_t)(b & 0x7fffffu) << 29)));
+}
+template <class T> __device__ __forceinline__ T from_f32(float f);
+template <> __device__ __forceinline__ float from_f32<float>(float f) { return f; }
+template <> __device__ __forceinline__ double from_f32<double>(float f) { return f32_to_f64(f); }
+
 // L2 bulk prefetch; the caller passes a 16-byte aligned address
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   if (bytes >= 16)
@@ -1128,14 +1146,14 @@ struct OpCsrRows {
 
   // one row's scatter into the warp's accumulator (columns distinct)
   template <class T>
-  static __device__ __forceinline__ void scatter(T *accw, const float4 &v, const int4 &c, T u,
+  static __device__ __forceinline__ void scatter(T *accw, const T (&v)[4], const int4 &c, T u,
                                                  bool act) {
     if (act) {
       const T a0 = accw[c.x], a1 = accw[c.y], a2 = accw[c.z], a3 = accw[c.w];
-      accw[c.x] = a0 + u * (T)v.x;
-      accw[c.y] = a1 + u * (T)v.y;
-      accw[c.z] = a2 + u * (T)v.z;
-      accw[c.w] = a3 + u * (T)v.w;
+      accw[c.x] = a0 + u * v[0];
+      accw[c.y] = a1 + u * v[1];
+      accw[c.z] = a2 + u * v[2];
+      accw[c.w] = a3 + u * v[3];
     }
     __syncwarp();
   }
@@ -1199,11 +1217,12 @@ struct OpCsrRows {
         w0lo = __ldg(a.rw2lo + r0 + ii);
         if (has1) w1lo = __ldg(a.rw2lo + r0 + ii + 1);
       }
+      // values in the product type, converted once for the dot and the scatter
+      const T x0[4] = {from_f32<T>(v0.x), from_f32<T>(v0.y), from_f32<T>(v0.z), from_f32<T>(v0.w)};
+      const T x1[4] = {from_f32<T>(v1.x), from_f32<T>(v1.y), from_f32<T>(v1.z), from_f32<T>(v1.w)};
       T d0 = (T)0, d1 = (T)0;
-      if (act0)
-        d0 = (T)v0.x * pw[c0.x] + (T)v0.y * pw[c0.y] + (T)v0.z * pw[c0.z] + (T)v0.w * pw[c0.w];
-      if (act1)
-        d1 = (T)v1.x * pw[c1.x] + (T)v1.y * pw[c1.y] + (T)v1.z * pw[c1.z] + (T)v1.w * pw[c1.w];
+      if (act0) d0 = x0[0] * pw[c0.x] + x0[1] * pw[c0.y] + x0[2] * pw[c0.z] + x0[3] * pw[c0.w];
+      if (act1) d1 = x1[0] * pw[c1.x] + x1[1] * pw[c1.y] + x1[2] * pw[c1.z] + x1[3] * pw[c1.w];
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         d0 += __shfl_xor_sync(0xffffffffu, d0, o);
@@ -1217,8 +1236,8 @@ struct OpCsrRows {
         u1 = OpCsrStaged::row_coef<T>(a, rd1, d1, ysrc, pold, beta, alo, na, arho, acs, aDl, aDu,
                                       apl, apu, afl, lane, pqt);
       if (lane == 0) pqt += u0 * d0 + u1 * d1;
-      scatter<T>(accw, v0, c0, u0, act0);
-      scatter<T>(accw, v1, c1, u1, act1);
+      scatter<T>(accw, x0, c0, u0, act0);
+      scatter<T>(accw, x1, c1, u1, act1);
     };
     int i = 2 * warp;
     const int stp = 2 * nw;
@@ -1881,7 +1900,10 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
   for (; q < order.size(); ++q) {
     const int j = order[q];
     int t = (int)std::floor(G * cost[j] / total);
-    t = std::min(t, hs[idx[j]]->W.G);
+    // at most two rows of H, A, C per warp of the team
+    const kq_problem *hj = hs[idx[j]];
+    t = (int)std::min<int64_t>(t, ceil_div64(hj->n + hj->m + hj->me, 32));
+    t = std::min(t, hj->num_sms);     // the problem's slot buffer holds up to num_sms CTAs
     if (t < 2 || used + t > G - 1) break;
     teams.push_back(TeamInfo{used, t, 0, 0});
     members.push_back({j});
@@ -2183,6 +2205,8 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
   int G = grid_ctas > 0 ? grid_ctas : sms;
   if (P.hkind == KQ_H_DENSE) {
     // small dense problems are latency-bound: fewer CTAs, cheaper barriers
+    // (two rows per warp; a single CTA was measured slower on n = 200: the
+    // row dots are then bound by one SM's FP64 and shuffle throughput)
     const int64_t rows = n + P.m + P.me;
     const int64_t want = ceil_div64(rows, (int64_t)(threads / 32) * 2);
     G = grid_ctas > 0 ? grid_ctas : (int)std::max<int64_t>(1, std::min<int64_t>(sms, want));
@@ -2385,7 +2409,9 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
     W.y32 = dalloc<float>(h, nkp);
     if (!W.p32_0 || !W.p32_1 || !W.y32) return kq_fail(h, KQ_ERR_OOM, "pcg FP32 copies");
   }
-  W.slots = dalloc<double>(h, 4 * G);
+  // per-CTA partial sums: sized for the widest team the batched solver may
+  // give this problem (up to every SM), not only for this problem's own grid
+  W.slots = dalloc<double>(h, 4 * (size_t)std::max(G, sms));
   W.bar = dalloc<unsigned int>(h, 2);
   W.err = dalloc<int>(h, 1);
   W.iters = dalloc<int>(h, 1);
