@@ -143,6 +143,7 @@ struct PcgWork {
   float *rval = nullptr;       // 4 * sum(len4)
   uint16_t *rcol = nullptr;    // 4 * sum(len4), 16-bit offsets from the CTA's window start
   int rws = 0;                 // stride of the per-warp accumulators (floats)
+  int stag_window = 200;       // FP32 pass stagnation window (iterations)
   int pf_dist = 0;             // L2 prefetch distance in warp steps (0: off)
   size_t smem_rows = 0;
   float *rw2lo = nullptr;      // nP: low part of the FP32-split row weight (FP64 products)

@@ -72,39 +72,6 @@ struct PcgArgs {
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 
 
-// Sum of G slot values in a fixed order (identical in every CTA).
-__device__ __forceinline__ double sum_slots(const double *s, int G, double *sh) {
-  double v = 0.0;
-  if (threadIdx.x < 32) {
-    for (int i = threadIdx.x; i < G; i += 32) v += __ldcg(s + i);
-    v = warp_sum(v);
-    if (threadIdx.x == 0) sh[0] = v;
-  }
-  __syncthreads();
-  v = sh[0];
-  __syncthreads();
-  return v;
-}
-
-// Two slot sums in one pass (same order as sum_slots).
-__device__ __forceinline__ void sum_slots2(const double *s0, const double *s1, int G, double *sh,
-                                           double &o0, double &o1) {
-  if (threadIdx.x < 32) {
-    double v0 = 0.0, v1 = 0.0;
-    for (int i = threadIdx.x; i < G; i += 32) {
-      v0 += __ldcg(s0 + i);
-      v1 += __ldcg(s1 + i);
-    }
-    v0 = warp_sum(v0);
-    v1 = warp_sum(v1);
-    if (threadIdx.x == 0) { sh[0] = v0; sh[1] = v1; }
-  }
-  __syncthreads();
-  o0 = sh[0];
-  o1 = sh[1];
-  __syncthreads();
-}
-
 // Threads that update the owned vector entries: one entry per thread where
 // the block allows, on as few warps as that takes.  The SM's FP64 pipe is
 // narrow, so warps without entries stay out of the FP64 reductions.
@@ -187,114 +154,6 @@ __device__ __forceinline__ double block_sum_buf(double v, double *buf, double *s
   __syncthreads();
   return r;
 }
-
-// ---------------------------------------------------------------- CSR (H = P'W2P, A = rows of P)
-struct OpCsr {
-  template <class T>
-  static __device__ double phaseA(const PcgArgs &a, const double *ysrc, const double *pold,
-                                  double *pnew, double beta, int64_t vb, int64_t ve,
-                                  unsigned char *smem) {
-    const DevProb &P = a.P;
-    const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nw = blockDim.x >> 5;
-    const int lo = a.win_lo[cta], hi = a.win_hi[cta];
-    const int wlen = hi - lo;
-    const bool win = wlen <= a.win_cap;
-    T *pw = reinterpret_cast<T *>(smem);
-    T *acc = pw + a.win_cap;
-    T *accg = reinterpret_cast<T *>(a.accx);
-    double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
-    if (win) {
-      for (int j = tid; j < wlen; j += blockDim.x) {
-        const int c = lo + j;
-        pw[j] = (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
-        acc[j] = (T)0;
-      }
-    }
-    __syncthreads();
-    const int64_t r0 = a.row_begin[cta], r1 = a.row_begin[cta + 1];
-    const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
-    for (int64_t r = r0 + warp; r < r1; r += nw) {
-      const int64_t s = P.rowptr[r], e = P.rowptr[r + 1];
-      T dot = (T)0;
-      const bool short_row = (e - s) <= 128;
-      float vv[4];
-      int cc[4];
-      if (short_row) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const int64_t kk = s + lane + 32 * q;
-          if (kk < e) {
-            vv[q] = ld_stream(P.val + kk);
-            cc[q] = ld_stream(P.col + kk);
-          } else {
-            vv[q] = 0.f;
-            cc[q] = -1;
-          }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (cc[q] >= 0) {
-            T pv = win ? pw[cc[q] - lo]
-                       : (T)(ldcg(ysrc + cc[q]) + beta * ldcg(pold + cc[q]));
-            dot += (T)vv[q] * pv;
-          }
-        }
-      } else {
-        for (int64_t kk = s + lane; kk < e; kk += 32) {
-          const int c = P.col[kk];
-          T pv = win ? pw[c - lo] : (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
-          dot += (T)P.val[kk] * pv;
-        }
-      }
-      dot = warp_sum(dot);
-      const double dd = (double)dot;
-      double ud = P.w2[r] * dd;
-      const int ai = P.prow2a[r];
-      if (ai >= 0) {
-        const double rho_a = P.rhoA[ai];
-        const double t = rho_a * dd;
-        const bool hl = P.hasl[ai] != 0, hu = P.hasu[ai] != 0;
-        const double pl = hl ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
-        const double pu = hu ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
-        const double coef = 2.0 * t * (a.cl[ai] + a.cu[ai]) + pl - pu;
-        ud += rho_a * coef;
-        if (lane == 0) {
-          const double ql = hl ? t + a.Dl[ai] * pl : 0.0;
-          const double qu = hu ? -t + a.Du[ai] * pu : 0.0;
-          a.qlam[P.me + ai] = ql;
-          a.qlam[P.me + P.m + ai] = qu;
-          pq += pl * ql + pu * qu;
-        }
-      }
-      if (lane == 0) pq += ud * dd;
-      const T u = (T)ud;
-      if (short_row) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          if (cc[q] >= 0) {
-            if (win) atomicAdd(acc + (cc[q] - lo), u * (T)vv[q]);
-            else atomicAdd(accg + cc[q], u * (T)vv[q]);
-          }
-        }
-      } else {
-        for (int64_t kk = s + lane; kk < e; kk += 32) {
-          const int c = P.col[kk];
-          if (win) atomicAdd(acc + (c - lo), u * (T)P.val[kk]);
-          else atomicAdd(accg + c, u * (T)P.val[kk]);
-        }
-      }
-    }
-    __syncthreads();
-    if (win) {
-      for (int j = tid; j < wlen; j += blockDim.x) {
-        const T v = acc[j];
-        if (v != (T)0) atomicAdd(accg + lo + j, v);
-      }
-    }
-    return pq;
-  }
-};
 
 // ---------------------------------------------------------------- DENSE (explicit H, dense A, C)
 // Eight consecutive entries of a row as T (16-byte loads; the caller checks
@@ -950,8 +809,7 @@ struct OpCsrStaged {
                                   unsigned char *smem, PipeState &ps, bool &ok) {
     const DevProb &P = a.P;
     const CsrLayout L = lay(a);
-    const int cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int nw = blockDim.x >> 5;
+    const int cta = blockIdx.x, tid = threadIdx.x;
     const int lo = a.win_lo[cta], hi = a.win_hi[cta];
     const int wlen = hi - lo;
     const bool win = wlen <= a.win_cap;
@@ -1703,7 +1561,7 @@ kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double t
   a.copy_piece = W.copy_piece;
   a.stages = W.stages;
   a.producer = W.producer;
-  a.stag_window = (prec == KQ_PREC_MIXED && !apply) ? 200 : 0;
+  a.stag_window = (prec == KQ_PREC_MIXED && !apply) ? W.stag_window : 0;
   a.coefA = W.coefA;
   a.rslot = W.rslot;
   a.rval4 = reinterpret_cast<const float4 *>(W.rval);
@@ -1956,7 +1814,7 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
     a.tol2 = tol[j] * tol[j]; a.maxit = maxit[j]; a.apply = apply;
     a.iters = B.d_iters + j; a.resn = B.d_resn + 2 * j;
     a.stages = 2; a.producer = 0; a.copy_piece = 16;
-    a.stag_window = (prec == KQ_PREC_MIXED && !apply) ? 200 : 0;
+    a.stag_window = (prec == KQ_PREC_MIXED && !apply) ? W.stag_window : 0;
     a.coefA = W.coefA;
     a.dinv = W.dinv;
     smem = std::max(smem, (size_t)2 * a.win_cap * (prec == KQ_PREC_MIXED ? sizeof(float) : sizeof(double)));
@@ -2365,6 +2223,12 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
   }
   W.G = G;
   W.threads = threads;
+  {
+    // FP32 passes end when |r| has not halved over this many iterations
+    // (KQ_STAG_WINDOW overrides, for tuning)
+    const char *sw = getenv("KQ_STAG_WINDOW");
+    W.stag_window = sw ? std::max(0, atoi(sw)) : 400;
+  }
   W.win_cap = win_cap;
   W.smem = smem;
   // verify co-residency for the cooperative launch
