@@ -245,9 +245,9 @@ def run_other(args):
             kq.qp_destroy(h)
         return 0
 
-    nqp = 128 if args.workload == "batch128" else 512
+    nqp = args.nqp if args.nqp > 0 else (128 if args.workload == "batch128" else 512)
     hi = 1024 if args.workload == "batch128" else 4096
-    sizes = qpgen.batch_sizes(nqp, 64, hi, size_seed=5 if nqp == 128 else 0)
+    sizes = qpgen.batch_sizes(nqp, 64, hi, size_seed=5 if args.workload == "batch128" else 0)
     qps = [qpgen.batch_qp(k, n, light=True) for k, n in enumerate(sizes)]
     for prec, name in ((kq.KQ_PREC_MIXED, "batched mixed"), (kq.KQ_PREC_F64, "batched f64")):
         b = kq.qp_create_batch(qps)
@@ -286,6 +286,8 @@ def main():
                     choices=["c1", "c0", "c2", "c4", "batch128", "batch512"],
                     help="c1 (default) is the benchmark; the others print one timing line "
                          "per form (plain FP64 / mixed / batched) on the other configurations")
+    ap.add_argument("--nqp", type=int, default=0,
+                    help="batch workloads: number of QPs (default 128 / 512)")
     ap.add_argument("--sequential", action="store_true",
                     help="batch workloads: also time plain FP64 one QP at a time")
     args = ap.parse_args()

@@ -1105,15 +1105,59 @@ struct OpCsrRows {
     ld_slots(i, sa0, sa1);
     ld_slots(i + stp, sb0, sb1);
     ld_slots(i + 2 * stp, sc0, sc1);
-    double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
-    ld_data(sa0, sa1, va0, va1, ca0, ca1);
-    ld_data(sb0, sb1, vb0, vb1, cb0, cb1);
+    double pq = 0.0;
     const float *p32o = (a.apply || sizeof(T) != 4) ? nullptr : p32_of(a, pold);
-    if (p32o && a.y32) {
+    constexpr int KW = 6;
+    if (p32o && a.y32 && wlen + 2 * na <= KW * (int)blockDim.x) {
       // window p from the FP32 copies of y and p_old (FP32 arithmetic: the
-      // product rounds p to FP32 anyway)
+      // product rounds p to FP32 anyway).  One index space: window columns,
+      // then the A rows' lower and upper entries.  The window loads are issued
+      // before the owned-entry update, so both take one memory round trip.
       const float b32 = (float)beta;
-      // one index space: window columns, then the A rows' lower and upper entries
+      const int tot = wlen + 2 * na;
+      float yv[KW], pv[KW];
+#pragma unroll
+      for (int k = 0; k < KW; ++k) {
+        const int j = tid + k * (int)blockDim.x;
+        yv[k] = 0.f;
+        pv[k] = 0.f;
+        if (j < tot) {
+          bool need = true;
+          int64_t ix;
+          if (j < wlen) {
+            ix = lo + j;
+          } else {
+            const int q = (j - wlen) >> 1, up = (j - wlen) & 1;
+            ix = (up ? up_off : lo_off) + alo + q;
+            need = (afl[q] & (up ? 2 : 1)) != 0;
+          }
+          if (need) {
+            yv[k] = __ldcg(a.y32 + ix);
+            pv[k] = __ldcg(p32o + ix);
+          }
+        }
+      }
+      ld_data(sa0, sa1, va0, va1, ca0, ca1);
+      ld_data(sb0, sb1, vb0, vb1, cb0, cb1);
+      pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
+#pragma unroll
+      for (int k = 0; k < KW; ++k) {
+        const int j = tid + k * (int)blockDim.x;
+        if (j < tot) {
+          const T v = (T)fmaf(b32, pv[k], yv[k]);
+          if (j < wlen) {
+            pw[j] = v;
+          } else {
+            const int q = (j - wlen) >> 1;
+            if ((j - wlen) & 1) apu[q] = v; else apl[q] = v;
+          }
+        }
+      }
+    } else if (p32o && a.y32) {
+      pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
+      ld_data(sa0, sa1, va0, va1, ca0, ca1);
+      ld_data(sb0, sb1, vb0, vb1, cb0, cb1);
+      const float b32 = (float)beta;
       for (int j = tid; j < wlen + 2 * na; j += blockDim.x) {
         if (j < wlen) {
           const int c = lo + j;
@@ -1126,6 +1170,9 @@ struct OpCsrRows {
         }
       }
     } else {
+      pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
+      ld_data(sa0, sa1, va0, va1, ca0, ca1);
+      ld_data(sb0, sb1, vb0, vb1, cb0, cb1);
       for (int j = tid; j < wlen; j += blockDim.x) {
         const int c = lo + j;
         pw[j] = (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
@@ -1333,6 +1380,20 @@ __device__ void pcg_body(const PcgArgs &a, const int cta, const int G, unsigned 
         }
       break;
     }
+    // the owned entries' operands do not depend on alpha: with at most one
+    // owned entry per vector thread, load them before the slot sum so that the
+    // two memory round trips overlap
+    const bool one_each = (ve - vb) <= (int64_t)vt;
+    const int64_t ci = vb + tid;
+    const bool mine = one_each && tid < vt && ci < ve;
+    double c_p = 0.0, c_q = 0.0, c_z = 0.0, c_r = 0.0, c_di = 0.0;
+    if (mine) {
+      c_p = pnew[ci];
+      c_q = (ci < n) ? (double)__ldcg(accg + ci) + a.dg[ci] * c_p : __ldcg(a.qlam + (ci - n));
+      c_z = a.z[ci];
+      c_r = a.r[ci];
+      c_di = a.dinv ? a.dinv[ci] : 1.0 / a.diag[ci];
+    }
     // alpha = rho / p'Kp (thread 0)
     {
       double pqt = 0.0, unused = 0.0;
@@ -1351,7 +1412,19 @@ __device__ void pcg_body(const PcgArgs &a, const int cta, const int G, unsigned 
       if (bad) break;
       // ---- phase C: vector updates on owned entries
       double part[2] = {0.0, 0.0};
-      if (tid < vt) {
+      if (one_each) {
+        if (mine) {
+          if (ci < n) accg[ci] = (T)0;
+          a.z[ci] = c_z + alpha * c_p;
+          const double ri = c_r - alpha * c_q;
+          a.r[ci] = ri;
+          const double yi = ri * c_di;
+          a.y[ci] = yi;
+          if (a.y32) a.y32[ci] = (float)yi;
+          part[0] = ri * ri;
+          part[1] = ri * yi;
+        }
+      } else if (tid < vt) {
         for (int64_t i = vb + tid; i < ve; i += vt) {
           const double pi = pnew[i];
           double qi;
