@@ -194,6 +194,17 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------- GPU arm
+def max_over_ranks(x: float, dist, device: str) -> float:
+    """The slowest rank's value (replicas: the job ends with the slowest one).
+    `dist` is torch.distributed or None (one process)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_other(args):
     """Time-to-1e-6 of the other configurations, plain FP64 against mixed
     (and batched), on one GPU.  One JSON line per form; the median of
@@ -367,10 +378,7 @@ def main():
         dist.barrier()
     ms_total = e0.elapsed_time(e1)
     t_step = ms_total / 1e3 / args.steps
-    if dist is not None:
-        t = torch.tensor([t_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = float(t.item())
+    t_step = max_over_ranks(t_step, dist, "cuda")
     s0 = stats[-1]
     prod = sum(s.pcg_products for s in stats)
     kms = sum(s.pcg_kernel_ms for s in stats)
@@ -423,10 +431,7 @@ def main():
         torch.cuda.synchronize()
         e2e_times.append(time.perf_counter() - t0)
     e2e = sum(e2e_times) / len(e2e_times)
-    if dist is not None:
-        t = torch.tensor([e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = float(t.item())
+    e2e = max_over_ranks(e2e, dist, "cuda")
 
     # ---- plain-FP64 form on the same problem, for the comparison
     cmp = None
