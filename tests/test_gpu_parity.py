@@ -27,6 +27,9 @@ PROBLEMS = {
     "csr_multichunk": lambda: qpgen.dose_qp(60000, 3000, 100, 300, 3000, seed=10,
                                             unit_dose=True),
     "csr_irregular": lambda: qpgen.irregular_lsq_qp(),
+    # rows of 0..128 nonzeros (empty rows, the longest rows of the
+    # register-streamed operator, lengths that need padding), scattered columns
+    "csr_short_irregular": lambda: qpgen.irregular_lsq_qp(max_len=128, long_rows=0, seed=13),
     "lowrank": lambda: qpgen.svm_qp(500, 16, seed=9),
 }
 
@@ -105,7 +108,7 @@ def test_kkt_apply(kq, name, prec, tol):
     assert np.all(out[pad] == 0.0)
 
 
-@pytest.mark.parametrize("name", ["csr", "csr_multichunk"])
+@pytest.mark.parametrize("name", ["csr", "csr_multichunk", "csr_short_irregular"])
 def test_kkt_apply_staged_operator(kq, name, monkeypatch):
     """FP32 products of short-row CSR problems normally run the
     register-streamed operator; KQ_STAGED=1 at create selects the staged
