@@ -31,6 +31,10 @@ sys.path.insert(0, ROOT)
 ALGO_BYTES_NOTE = ("per K*v product: nnz*(4 B value + 4 B column) + (rows+1)*4 B row pointer "
                    "+ rows*4 B weight")
 WORKLOAD = "dose_qp_200k_x_20k_nnz2e7"
+METRIC = "time-to-1e-6 IPM solve (dose-shaped QP, PCG on the doubly augmented KKT system)"
+# the benchmark workload (both arms)
+CONFIG = {"workload": WORKLOAD, "rows": 200_000, "n": 20_000, "nnz": 20_000_000,
+          "dose_limit_rows": 10_000, "l2": "inputs larger than L2 (P is 160 MB > 129 MB)"}
 COUNTS_FILE = os.path.join(ROOT, "profiles", "dose200k_counts.json")
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "pcg_csr_dose200k_traffic.json")
 
@@ -181,11 +185,11 @@ def run_reference(args):
         last = cpu_baseline_line(ipm_iters, products, nit=10)
         vals.append(last["value"])
     v = sum(vals) / len(vals)
-    line = {"impl": "reference", "metric": "time-to-1e-6 IPM solve", "value": v, "unit": "s",
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": v * 1e3, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "counts_from": src},
+            "config": dict(CONFIG, precision="f64", parallelism="single-gpu", counts_from=src),
             "cpu_baseline": {"kind": "oracle", "cores": 1, "sample": last["sample"], "value": v,
                              "unit": "s"},
             "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -466,16 +470,15 @@ def main():
 
     if rank == 0:
         line = {
-            "metric": "time-to-1e-6 IPM solve (dose-shaped QP, PCG on the doubly augmented KKT system)",
+            "metric": METRIC,
             "value": t_step, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32-matvec/f64" if prec == kq.KQ_PREC_MIXED else "f64",
             "data": "synthetic (seeded generator, seed 1)",
-            "config": {"workload": WORKLOAD, "rows": qp.P.shape[0], "n": qp.n, "nnz": qp.P.nnz,
-                       "dose_limit_rows": m, "precision": args.precision,
-                       "l2": "inputs larger than L2 (P is 160 MB > 129 MB)",
-                       "parallelism": "replicas" if world > 1 else "single-gpu"},
+            "config": dict(CONFIG, rows=qp.P.shape[0], n=qp.n, nnz=qp.P.nnz, dose_limit_rows=m,
+                           precision=args.precision,
+                           parallelism="replicas" if world > 1 else "single-gpu"),
             "ipm_iters": s0.ipm_iters, "pcg_iters": int(s0.pcg_iters),
             "pcg_products": int(s0.pcg_products), "pcg_iters_f64": int(s0.pcg_iters_f64),
             "pcg_maxit_hits": s0.pcg_maxit_hits,
