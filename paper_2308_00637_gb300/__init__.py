@@ -403,7 +403,8 @@ def qp_layer(qp, p, lA, uA, b, opts: Optional[KqIpmOpts] = None):
 
 
 def solve(qp, opts: Optional[KqIpmOpts] = None, allow=(KQ_OK,)):
-    """Create, solve and return (status, stats, x, multipliers dict)."""
+    """Create, solve, destroy; returns (status, stats, out) with out a dict of
+    host arrays x, lam_lA, lam_uA, lam_lx, lam_ux, lam_e (original units)."""
     h = create_from(qp)
     n, m, me = h.n, h.m, h.me
     out = {k: np.zeros(s) for k, s in (("x", n), ("lam_lA", m), ("lam_uA", m), ("lam_lx", n),
