@@ -185,6 +185,7 @@ struct kq_problem {
   int num_sms = 0;
   double timeout_s = 2.0;
   long long launches = 0;       // kernels launched by this handle
+  float last_kernel_ms = 0.f;   // device time of this handle's last persistent PCG launch
   long long pcg_launches = 0;   // persistent PCG launches (solve + apply)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };
@@ -205,7 +206,7 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
                     kq_pcg_stats *st);
 // out = K v in FP64 (prec = KQ_PREC_F64) or mixed arithmetic.
 kq_status pcg_apply(kq_problem *h, const double *v, double *out, int prec, float *ms);
-double pcg_last_kernel_ms();
+double pcg_last_kernel_ms(const kq_problem *h);
 // Work buffers of one persistent PCG launch, provided by the caller.
 struct PcgRawWork {
   double *r, *y, *pb0, *pb1, *qlam, *slots, *resn;

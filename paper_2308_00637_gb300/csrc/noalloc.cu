@@ -32,7 +32,7 @@ static __device__ __align__(256) double g_kq_static_scratch[KQ_STATIC_DOUBLES];
 // Device address of the array, looked up once per device (host code must not
 // use the symbol itself: in host code it is only a stand-in).
 double *g_scratch_addr[64] = {nullptr};
-std::string g_static_err;
+thread_local std::string g_static_err;
 
 // Jacobi diagonal of K (Eq. (9)) for dense H and A with all rows two-sided:
 // diag_x = H_jj + dg_j + 2 sum_a A_aj^2 (1/Dl_a + 1/Du_a), diag_lam = (Dl, Du);

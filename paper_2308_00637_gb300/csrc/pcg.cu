@@ -1596,7 +1596,6 @@ template <class T> KFun pick_kernel(const DevProb &P) {
   return a64 ? pcg_kernel<OpDense<__nv_bfloat16, double>, T> : pcg_kernel<OpDense<__nv_bfloat16, float>, T>;
 }
 
-float g_last_ms = 0.f;
 
 RowDesc split_w2(int32_t off, int32_t a, double w2) {
   const float hi = (float)w2;
@@ -1671,7 +1670,7 @@ kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double t
   KQ_CUDA(h, cudaMemcpyAsync(W.h_pinned + 1, W.iters, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   KQ_CUDA(h, cudaMemcpyAsync(W.h_pinned + 2, W.resn, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
   KQ_CUDA(h, cudaStreamSynchronize(h->stream));
-  KQ_CUDA(h, cudaEventElapsedTime(&g_last_ms, h->ev0, h->ev1));
+  KQ_CUDA(h, cudaEventElapsedTime(&h->last_kernel_ms, h->ev0, h->ev1));
   const int err = W.h_pinned[0];
   if (iters_out) *iters_out = W.h_pinned[1];
   double rb[2];
@@ -1958,7 +1957,7 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
   return KQ_OK;
 }
 
-double pcg_last_kernel_ms() { return g_last_ms; }
+double pcg_last_kernel_ms(const kq_problem *h) { return h->last_kernel_ms; }
 
 // Fill of the register-streamed layout, one warp per row of P.  The row's
 // nonzeros are ranked by (multiplicity of their bank in the row, descending;
@@ -2364,7 +2363,7 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
 
 kq_status pcg_apply(kq_problem *h, const double *v, double *out, int prec, float *ms) {
   kq_status st = launch(h, prec, v, out, 0.0, 0, 1, nullptr, nullptr, nullptr);
-  if (ms) *ms = g_last_ms;
+  if (ms) *ms = h->last_kernel_ms;
   return st;
 }
 
@@ -2401,12 +2400,12 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
     if (budget <= 0) break;
     int it = 0;
     rc = launch(h, prec, res, dz, rel, budget, 0, &it, nullptr, nullptr);
-    s.kernel_ms += g_last_ms;
+    s.kernel_ms += h->last_kernel_ms;
     total += it;
     if (prec == KQ_PREC_F64) {
       s.iters_f64 += it;
       s.products_f64 += it;
-      s.kernel_ms_f64 += g_last_ms;
+      s.kernel_ms_f64 += h->last_kernel_ms;
       s.launches_f64 += 1;
     }
     s.passes++;
