@@ -7,7 +7,8 @@
 * c1 (dose QP, 2e7 nnz, the benchmark workload): properties that hold at any
   size -- KKT_rel <= 1e-6 evaluated by the oracle's metric code in FP64 from
   the original data, mu_final = 1e-7, and the mixed and FP64 solutions agree
-  on the objective to 1e-6.
+  on the objective to 1e-6; and K*v of Eq. (9) at full size, every entry,
+  against the oracle's product.
 """
 import numpy as np
 import pytest
@@ -69,3 +70,29 @@ def test_config1_properties(kq):
         assert np.min(out["x"]) >= -1e-9
         objs.append(met["objective"])
     assert abs(objs[0] - objs[1]) <= 1e-6 * (1 + abs(objs[1]))
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 1e-5)], ids=["f64", "mixed"])
+def test_config1_kkt_apply_full_size(kq, prec, tol):
+    """The benchmark workload at full size, in the benchmark's launch
+    configuration (one CTA per SM, the register-streamed operator): K*v of
+    Eq. (9) at a seeded interior iterate against the oracle's matrix-free
+    product, every entry.  Tolerances as in the small parity tests (FP64:
+    a different summation order; FP32 products: unit roundoff 6e-8 over at
+    most a few hundred terms per entry)."""
+    from oracle import ipm as I
+    from tests.gpu_helpers import from_padded, random_state, relerr, set_gpu_state, to_padded
+    qp = qpgen.config1()
+    S = I.scale(qp)
+    st = random_state(S, 7)
+    mu = 0.01
+    h = kq.create_from(qp)
+    set_gpu_state(kq, h, S, st, mu)
+    r = I.residuals(S, st, mu)
+    dg, D, _, _ = I.reduced_system(S, st, r, mu)
+    v = np.random.default_rng(11).standard_normal(S.NK)
+    ref = I.kkt_apply(S, dg, D, v)
+    out = np.zeros(h.nkp)
+    kq.kkt_apply(h, to_padded(S, v), out, prec)
+    assert relerr(from_padded(S, out), ref) <= tol
+    kq.qp_destroy(h)
