@@ -7,8 +7,9 @@
 * c1 (dose QP, 2e7 nnz, the benchmark workload): properties that hold at any
   size -- KKT_rel <= 1e-6 evaluated by the oracle's metric code in FP64 from
   the original data, mu_final = 1e-7, and the mixed and FP64 solutions agree
-  on the objective to 1e-6; and K*v of Eq. (9) at full size, every entry,
-  against the oracle's product.
+  on the objective to 1e-6; K*v of Eq. (9) at full size, every entry,
+  against the oracle's product; and one full-size Newton system solved to the
+  paper's tolerance, checked through the oracle's FP64 residual.
 """
 import numpy as np
 import pytest
@@ -95,4 +96,30 @@ def test_config1_kkt_apply_full_size(kq, prec, tol):
     out = np.zeros(h.nkp)
     kq.kkt_apply(h, to_padded(S, v), out, prec)
     assert relerr(from_padded(S, out), ref) <= tol
+    kq.qp_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["f64", "mixed"])
+def test_config1_pcg_solve_full_size(kq, prec):
+    """One Newton system of the benchmark workload at full size (the initial
+    iterate, mu = 1) solved by the GPU PCG with the paper's settings (1e-7
+    relative, at most 5000 iterations); its FP64 residual, evaluated by the
+    oracle's matrix-free product, meets the tolerance."""
+    from oracle import ipm as I
+    from tests.gpu_helpers import from_padded, set_gpu_state, to_padded
+    qp = qpgen.config1()
+    S = I.scale(qp)
+    st = I.initial_point(S)
+    mu = 1.0
+    h = kq.create_from(qp)
+    set_gpu_state(kq, h, S, st, mu)
+    r = I.residuals(S, st, mu)
+    dg, D, r1, r2 = I.reduced_system(S, st, r, mu)
+    rhs = I.doubly_augmented_rhs(S, D, r1, r2)
+    sol = np.zeros(h.nkp)
+    rc, stt = kq.kkt_pcg_solve(h, to_padded(S, rhs), sol, kq.default_pcg_opts(precision=prec))
+    z = from_padded(S, sol)
+    res = np.linalg.norm(rhs - I.kkt_apply(S, dg, D, z)) / np.linalg.norm(rhs)
+    print("c1 full-size PCG prec", prec, stt.as_dict(), "residual %.2e" % res)
+    assert rc == kq.KQ_OK and res <= 1e-7 * 1.01
     kq.qp_destroy(h)
