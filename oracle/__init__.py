@@ -15,7 +15,7 @@ the equations state.  It shares no code with the GPU path.
 from .ipm import (  # noqa: F401
     Scaled, State, scale, initial_point, residuals, residual_norm, reduced_system,
     doubly_augmented_matrix, doubly_augmented_rhs, kkt_apply, jacobi_diagonal,
-    full_newton_matrix, newton_direct, recover_step, ratio_test, ipm_solve,
+    full_newton_matrix, newton_direct, recover_step, ratio_test, ipm_solve, ipm_iterate,
     pcg_reference, adjoint_solve, unscale_solution, IpmResult,
 )
 from .metrics import kkt_metrics, objective, full_multipliers  # noqa: F401

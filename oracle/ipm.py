@@ -553,9 +553,11 @@ class IpmResult:
     log: list
 
 
-def ipm_solve(qp, gamma=0.99, mu_tol=1e-6, maxit=200, solver="auto",
-              pcg_tol=1e-7, pcg_maxit=5000, max_iters=None, log=False) -> IpmResult:
-    """Algorithm 1 with a direct (default) or reference-PCG Newton solve."""
+def ipm_iterate(qp, gamma=0.99, mu_tol=1e-6, maxit=200, solver="auto",
+                pcg_tol=1e-7, pcg_maxit=5000, max_iters=None, log=False):
+    """Algorithm 1 as a generator: yields a dict after every IPM iteration
+    (its number, mu, ||r||, step lengths, and the iterate so far); the last
+    dict carries the final result under "result".  ipm_solve consumes it."""
     S = scale(qp)
     st = initial_point(S)
     k = 0                       # mu = 10^-k
@@ -586,16 +588,35 @@ def ipm_solve(qp, gamma=0.99, mu_tol=1e-6, maxit=200, solver="auto",
             pr, du, co = infeasibilities(r)
             hist.append(dict(it=it, mu=mu, res=rn, alpha_x=ax, alpha_lam=al,
                              primal=pr, dual=du, compl=co, **info))
+        step = {"it": it, "mu": mu, "res": rn, "alpha_x": ax, "alpha_lam": al}
+        done = False
         if rn < mu:
             if mu < mu_tol:
                 status = "converged"
-                break
-            k += 1
-            mu = 10.0 ** (-k)
-            r = residuals(S, st, mu)
+                done = True
+            else:
+                k += 1
+                mu = 10.0 ** (-k)
+                r = residuals(S, st, mu)
+        if done or it == limit:
+            x, lam, s = unscale_solution(S, st)
+            step["result"] = IpmResult(status=status, iters=it, mu=mu, x=x, lam=lam, s=s,
+                                       state=st, scaled=S, log=hist)
+            yield step
+            return
+        yield step
     x, lam, s = unscale_solution(S, st)
-    return IpmResult(status=status, iters=it, mu=mu, x=x, lam=lam, s=s, state=st,
-                     scaled=S, log=hist)
+    yield {"it": it, "mu": mu, "result": IpmResult(status=status, iters=it, mu=mu, x=x, lam=lam,
+                                                   s=s, state=st, scaled=S, log=hist)}
+
+
+def ipm_solve(qp, gamma=0.99, mu_tol=1e-6, maxit=200, solver="auto",
+              pcg_tol=1e-7, pcg_maxit=5000, max_iters=None, log=False) -> IpmResult:
+    """Algorithm 1 with a direct (default) or reference-PCG Newton solve."""
+    last = None
+    for last in ipm_iterate(qp, gamma, mu_tol, maxit, solver, pcg_tol, pcg_maxit, max_iters, log):
+        pass
+    return last["result"]
 
 
 def unscale_solution(S: Scaled, st: State):

@@ -17,6 +17,9 @@ evaluated in float64 from the original problem data and a candidate solution
                of a multiplier relative to the gradient scale and a slack
                relative to the primal scale, so it is invariant to scaling the
                objective or the rows;
+* gap        = sum of lam_i * shat_i + lam_e'(Cx - b): the primal-dual gap
+               f(x) - g(lam) at a dual-feasible point (g the Lagrangian dual
+               function); gap_rel = |gap| / (1 + |f|);
 * kkt_rel    = max(primal_rel, dual_rel): the residuals the acceptance gate
                (1e-6) applies to.  Complementarity is set by the final barrier
                parameter through the method's internal scaling (lam*s = mu in
@@ -103,8 +106,18 @@ def kkt_metrics(qp, x, lam_lA, lam_uA, lam_lx, lam_ux, lam_e):
     comp.append(float(np.max(np.abs(np.asarray(lam_lx) * slx))))
     comp.append(float(np.max(np.abs(np.asarray(lam_ux) * sux))))
     compl = max(comp) / ((1.0 + float(np.max(np.abs(x)))) * scale)
+    # duality gap: sum of multiplier x slack over every inequality (shat from x)
+    # plus lam_e'(Cx - b); equals f(x) - g(lam) + x'r_H, g the Lagrangian dual
+    # function, so at a dual-feasible point (r_H = 0) it is the primal-dual gap
+    gap = 0.0
+    if m:
+        gap += float(np.sum(np.asarray(lam_lA) * sl) + np.sum(np.asarray(lam_uA) * su))
+    gap += float(np.sum(np.asarray(lam_lx) * slx) + np.sum(np.asarray(lam_ux) * sux))
+    if me:
+        gap += float(np.asarray(lam_e, float) @ (C @ x - qp.b))
     return {"primal_rel": primal, "dual_rel": dual, "compl_rel": compl,
-            "kkt_rel": max(primal, dual), "objective": f}
+            "kkt_rel": max(primal, dual), "objective": f, "gap": gap,
+            "gap_rel": abs(gap) / (1.0 + abs(f))}
 
 
 def full_multipliers(res_or_S, lam: dict, qp):

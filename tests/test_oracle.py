@@ -329,3 +329,164 @@ def test_metrics_flag_bad_solution():
     good = oracle.kkt_metrics(qp, res.x, lA, uA, lx, ux, le)
     bad = oracle.kkt_metrics(qp, res.x + 1e-3, lA, uA, lx, ux, le)
     assert good["kkt_rel"] <= 1e-6 < bad["kkt_rel"]
+
+
+# ---------------------------------------------------------------- hand-computed worked examples
+def _worked_qp():
+    """n = 2, one two-sided general row (norm 5), one equality row (norm 2),
+    x1 in [-1, 1], x2 >= 0.  max H_ii = 0.5 and |p|_inf = 0.5, so the
+    objective scale sigma is 1; the rows are divided by 5 and by 2."""
+    return qpgen.QPData(n=2, hkind="dense", p=np.array([0.5, -0.25]),
+                        H=np.array([[0.5, 0.0], [0.0, 0.25]]), akind="dense",
+                        A=np.array([[3.0, 4.0]]), lA=np.array([-5.0]), uA=np.array([10.0]),
+                        C=np.array([[0.0, 2.0]]), b=np.array([2.0]),
+                        lx=np.array([-1.0, 0.0]), ux=np.array([1.0, np.inf]))
+
+
+def _worked_state():
+    """Scaled units.  x = (0.5, 1); row slacks 1.5 / 0.5 with multipliers 2 / 1;
+    bound slacks (1, 2) on the lower bounds of x1, x2 and 0.25 on the upper
+    bound of x1, with multipliers (0.5, 0.25) and 4; lam_e = 0.5."""
+    return I.State(x=np.array([0.5, 1.0]), s_lA=np.array([1.5]), s_uA=np.array([0.5]),
+                   s_lx=np.array([1.0, 2.0]), s_ux=np.array([0.25]), lam_e=np.array([0.5]),
+                   lam_lA=np.array([2.0]), lam_uA=np.array([1.0]),
+                   lam_lx=np.array([0.5, 0.25]), lam_ux=np.array([4.0]))
+
+
+# Every block of the right-hand side of Eq. (7) for the worked example at
+# mu = 0.1, worked out by hand from Eq. (3) (readings R1: r_uA = -Ax - s_u + u,
+# r_c2 = lam_u s_u - mu, stationarity term -C' lam_e):
+#   scaled A x = 0.6*0.5 + 0.8*1 = 1.1;  H x + p = (0.75, 0);  A'(lam_l - lam_u) = (0.6, 0.8)
+#   r_H  = (0.75 - 0.6 - 0 - 0.5 + 4,  0 - 0.8 - 0.5 - 0.25) = (3.65, -1.55)
+#   r_e  = 1 - 1 + 0.1*0.5 = 0.05
+#   r_lA = 1.1 - 1.5 + 1 = 0.6          r_uA = -1.1 - 0.5 + 2 = 0.4
+#   r_lx = (0.5 - 1 + 1, 1 - 2 - 0) = (0.5, -1)     r_ux = -0.5 - 0.25 + 1 = 0.25
+#   r_c1 = 2*1.5 - 0.1 = 2.9            r_c2 = 1*0.5 - 0.1 = 0.4
+#   r_c3 = (0.5 - 0.1, 0.5 - 0.1)       r_c4 = 4*0.25 - 0.1 = 0.9
+# sum of squares = 15.725 + 0.0025 + 0.36 + 0.16 + 1.25 + 0.0625 + 8.41 + 0.16 + 0.32 + 0.81
+#                = 27.26
+WORKED_BLOCKS = {"r_H": [3.65, -1.55], "r_e": [0.05], "r_lA": [0.6], "r_uA": [0.4],
+                 "r_lx": [0.5, -1.0], "r_ux": [0.25], "r_c1": [2.9], "r_c2": [0.4],
+                 "r_c3": [0.4, 0.4], "r_c4": [0.9]}
+WORKED_NORM2 = 27.26
+
+
+def _residual_norm_pinned(norm_fn, resid_fn):
+    S = I.scale(_worked_qp())
+    assert S.sigma == 1.0
+    r = resid_fn(S, _worked_state(), 0.1)
+    blocks_ok = all(np.allclose(r[k], v, rtol=0, atol=1e-14) for k, v in WORKED_BLOCKS.items())
+    return blocks_ok and abs(norm_fn(r) - np.sqrt(WORKED_NORM2)) <= 1e-13
+
+
+def test_residual_norm_worked_example():
+    """R8: ||r||_2 over all ten blocks of Eq. (7) at the current mu, on a
+    worked example computed by hand (including the row and equality scaling
+    of R9)."""
+    assert _residual_norm_pinned(I.residual_norm, I.residuals)
+
+
+def test_residual_norm_pin_catches_planted_mistakes():
+    """Plausible mistakes in the residual norm or in the blocks it sums are
+    caught by the worked example: complementarity blocks dropped, mu left out
+    of r_c, the penalty term mu*lam_e dropped from r_e, the r_uA slack sign of
+    the printed Eq. (3)."""
+    def drop_compl(r):
+        return float(np.sqrt(sum(float(r[k] @ r[k]) for k in I.RES_KEYS[:6])))
+
+    def resid_no_mu(S, st, mu):
+        return I.residuals(S, st, 0.0)
+
+    def resid_no_penalty(S, st, mu):
+        r = I.residuals(S, st, mu)
+        r["r_e"] = r["r_e"] - mu * st.lam_e
+        return r
+
+    def resid_printed_sign(S, st, mu):
+        r = I.residuals(S, st, mu)
+        r["r_uA"] = r["r_uA"] + 2.0 * st.s_uA
+        return r
+    assert not _residual_norm_pinned(drop_compl, I.residuals)
+    for bad in (resid_no_mu, resid_no_penalty, resid_printed_sign):
+        assert not _residual_norm_pinned(I.residual_norm, bad)
+
+
+def _ip_qp():
+    """Four variables with every bound pattern: [-1, 3] (midpoint 1), [2, inf)
+    (2 + 1), (-inf, 5] (5 - 1), free (0), plus [-0.25, 0.25] (midpoint 0, gap
+    below 2 so both slacks are clipped to 1).  Rows (original units):
+    a1 = e1 with lA = -2; a2 = (0, 0, 3, 0, 4, ...) / norm 5 with lA = 10 (scaled 2)
+    and uA = 50 (scaled 10); a3 = (0, 4, 0, 3, 0) norm 5 with uA = 14.5 (scaled 2.9).
+    One equality row."""
+    n = 5
+    A = np.array([[1.0, 0, 0, 0, 0], [0, 0, 3.0, 0, 4.0], [0, 4.0, 0, 3.0, 0]])
+    return qpgen.QPData(n=n, hkind="dense", p=np.zeros(n), H=np.eye(n), akind="dense", A=A,
+                        lA=np.array([-2.0, 10.0, -np.inf]), uA=np.array([np.inf, 50.0, 14.5]),
+                        C=np.array([[1.0, 1.0, 1.0, 1.0, 1.0]]), b=np.array([0.0]),
+                        lx=np.array([-1.0, 2.0, -np.inf, -np.inf, -0.25]),
+                        ux=np.array([3.0, np.inf, 5.0, np.inf, 0.25]))
+
+
+# R6 by hand for _ip_qp: x0 = (1, 3, 4, 0, 0).  Scaled row values at x0:
+#   a1: 1 (lower -2: slack max(3, 1) = 3)
+#   a2: (3*4 + 4*0)/5 = 2.4 (lower 2: max(0.4, 1) = 1; upper 10: max(7.6, 1) = 7.6)
+#   a3: (4*3 + 3*0)/5 = 2.4 (upper 2.9: max(0.5, 1) = 1)
+# bound slacks: lower bounds of x1, x2, x5: max(2, 1), max(1, 1), max(0.25, 1);
+# upper bounds of x1, x3, x5: max(2, 1), max(1, 1), max(0.25, 1)
+IP_EXPECT = {"x": [1.0, 3.0, 4.0, 0.0, 0.0], "s_lA": [3.0, 1.0], "s_uA": [7.6, 1.0],
+             "s_lx": [2.0, 1.0, 1.0], "s_ux": [2.0, 1.0, 1.0], "lam_lA": [1.0, 1.0],
+             "lam_uA": [1.0, 1.0], "lam_lx": [1.0, 1.0, 1.0], "lam_ux": [1.0, 1.0, 1.0],
+             "lam_e": [0.0]}
+
+
+def _initial_point_pinned(fn):
+    st = fn(I.scale(_ip_qp()))
+    return all(np.shape(getattr(st, k)) == np.shape(v)
+               and np.allclose(getattr(st, k), v, rtol=0, atol=1e-14) for k, v in IP_EXPECT.items())
+
+
+def test_initial_point_worked_example():
+    """R6 on a worked example with every bound pattern, computed by hand."""
+    assert _initial_point_pinned(I.initial_point)
+
+
+def test_initial_point_pin_catches_planted_mistakes():
+    """A slack without the max(., 1) clip, l + 1 used for a two-sided bound,
+    and unit multipliers on absent bounds all fail the worked example."""
+    def no_clip(S):
+        st = I.initial_point(S)
+        Ax = S.A @ st.x
+        st.s_lA = Ax[S.L] - S.lA[S.L]
+        return st
+
+    def lower_plus_one(S):
+        st = I.initial_point(S)
+        both = np.isfinite(S.lx) & np.isfinite(S.ux)
+        st.x = st.x.copy()
+        st.x[both] = S.lx[both] + 1.0
+        return st
+
+    def all_multipliers(S):
+        st = I.initial_point(S)
+        st.lam_lx = np.ones(S.n)
+        return st
+    for bad in (no_clip, lower_plus_one, all_multipliers):
+        assert not _initial_point_pinned(bad)
+
+
+def test_duality_gap_is_primal_minus_dual_objective():
+    """The reported gap equals f(x) - g(lam) + x'r_H, with the Lagrangian dual
+    function of Eq. (1) written out: g = -1/2 x'Hx + lam_lA'lA - lam_uA'uA +
+    lam_lx'lx - lam_ux'ux + lam_e'b (at x satisfying stationarity up to r_H)."""
+    qp = qpgen.tiny_qp(5, 3, 7, me=1)
+    res = oracle.ipm_solve(qp)
+    lA, uA, lx, ux, le = full_multipliers(res.scaled, res.lam, qp)
+    x = res.x
+    H = qp.H_dense()
+    met = oracle.kkt_metrics(qp, x, lA, uA, lx, ux, le)
+    rH = H @ x + qp.p - qp.A.T @ (lA - uA) - (lx - ux) - qp.C.T @ le
+    f = 0.5 * x @ H @ x + qp.p @ x
+    g = -0.5 * x @ H @ x + lA @ qp.lA - uA @ qp.uA + lx @ qp.lx - ux @ qp.ux + le @ qp.b
+    assert met["gap"] == pytest.approx(f - g + x @ rH, rel=1e-10, abs=1e-12)
+    # converged: the gap is of the order of the final barrier parameter
+    assert 0.0 < met["gap"] < 1e-5
