@@ -60,8 +60,11 @@ enum {
 enum { KQ_H_DENSE = 0,     /* explicit symmetric n x n, row-major              */
        KQ_H_CSR_LSQ = 1,   /* H = 2 P' diag(w) P, P CSR (rows x n)             */
        KQ_H_LOWRANK = 2 }; /* H = Z Z', Z dense n x k row-major                */
-/* constraint-matrix kinds */
-enum { KQ_A_NONE = 0, KQ_A_DENSE = 1, KQ_A_ROWS_OF_P = 3 };
+/* constraint-matrix kinds (the general rows l <= A x <= u of Eq. (1)) */
+enum { KQ_A_NONE = 0,      /* no general rows                                   */
+       KQ_A_DENSE = 1,     /* m x n row-major                                   */
+       KQ_A_CSR = 2,       /* m x n CSR (val, col, rowptr), any H kind          */
+       KQ_A_ROWS_OF_P = 3 };/* rows of the CSR_LSQ operator's P (dose limits)  */
 /* storage types */
 enum { KQ_F64 = 0, KQ_F32 = 1, KQ_BF16 = 2 };
 /* arithmetic of the K products inside PCG */
@@ -83,10 +86,14 @@ typedef struct {
 
 typedef struct {
   int kind;                /* KQ_A_*                                            */
-  int dtype;               /* DENSE: KQ_F64 or KQ_F32                           */
+  int dtype;               /* DENSE, CSR: KQ_F64 or KQ_F32                      */
   int64_t m;               /* number of rows                                    */
-  const void *val;         /* DENSE: m x n row-major                            */
+  const void *val;         /* DENSE: m x n row-major; CSR: nnz values           */
   const int32_t *rows;     /* ROWS_OF_P: row ids into P (m), strictly increasing*/
+  int64_t nnz;             /* CSR: nonzeros                                     */
+  const int32_t *col;      /* CSR: column of each nonzero (0 <= col < n)        */
+  const int64_t *rowptr;   /* CSR: row pointers (m + 1, rowptr[0] = 0,          */
+                           /*      rowptr[m] = nnz, non-decreasing)             */
 } kq_amat;
 
 typedef struct {
@@ -157,10 +164,14 @@ void kq_default_pcg_opts(kq_pcg_opts *o);
  *  me     equality rows; C dense me x n row-major FP64 and b (me); NULL if me=0
  *  lx,ux  variable bounds (n each, may be NULL = free)
  *  stream cudaStream_t (as void*), NULL for the default stream
- * Supported: DENSE H (F64/F32/BF16) with A NONE or DENSE (F64/F32) and any me;
- * CSR_LSQ H (F32 values) with A NONE or ROWS_OF_P and me = 0; LOWRANK H
- * (F32/F64) with A NONE and any me.  Errors: KQ_ERR_ARG for bad sizes or an
- * unsupported combination, KQ_ERR_OOM, KQ_ERR_CUDA.  *out is NULL on error. */
+ * Supported: every H kind (DENSE F64/F32/BF16, CSR_LSQ with F32 values,
+ * LOWRANK F32/F64) with A NONE or CSR (F64/F32 values) and any number of
+ * equality rows; DENSE A (F64/F32) with DENSE H; ROWS_OF_P with CSR_LSQ H.
+ * CSR structures (P and A) are checked on the device: a row pointer out of
+ * order or a column outside [0, n) gives KQ_ERR_ARG.  A NaN or infinity in p
+ * or on the diagonal of H gives KQ_ERR_NUMERIC.  Other errors: KQ_ERR_ARG for
+ * bad sizes or an unsupported combination, KQ_ERR_OOM, KQ_ERR_CUDA.  *out is
+ * NULL on error. */
 kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
                     const kq_amat *A, const double *lA, const double *uA,
                     int64_t me, const double *C, const double *b,
@@ -270,6 +281,13 @@ kq_status qp_create_batch(kq_batch *out, int nqp, const kq_qp_desc *descs, void 
 kq_status ipm_solve_batch(kq_batch b, const kq_ipm_opts *opts, double *const *x, int *status,
                           kq_batch_stats *stats);
 kq_status qp_batch_info(kq_batch b, int *nqp, int64_t *n);
+/* The current iterate of QP i of the batch (after ipm_solve_batch: its final
+ * iterate) in original units, as ipm_solve returns it: x (n_i), lam_lA, lam_uA
+ * (m_i, zero where the bound is absent), lam_lx, lam_ux (n_i), lam_e (me_i).
+ * Any pointer may be NULL; host or device memory.  Synchronises the batch's
+ * stream. */
+kq_status qp_batch_solution(kq_batch b, int i, double *x, double *lam_lA, double *lam_uA,
+                            double *lam_lx, double *lam_ux, double *lam_e);
 const char *qp_batch_last_error(kq_batch b);
 const char *kq_batch_error(void);
 void qp_batch_destroy(kq_batch b);
@@ -289,15 +307,28 @@ void qp_batch_destroy(kq_batch b);
  *  rhs, sol  n + 2m (device), layout [x | lam_l | lam_u]; z0 = 0
  *  tol       relative unpreconditioned residual; maxit iterations
  *  stream    cudaStream_t or NULL; *iters, *rel_res (recursive) may be NULL
- * The first call on a device looks up the array's device address; make that
- * first call before any stream capture.  The array keeps the last call's
- * contents (its counters are cleared on entry), so calls that overlap on the
- * GPU race: serialise them.  KQ_WARN_PCG_MAXIT if the tolerance was not met;
- * errors are reported by kq_global_error(). */
+ * All pointers must be device memory.  The first call on a device looks up
+ * the array's device address; make that first call before any stream capture.
+ * Every call waits for its stream (it reads status words back) before it
+ * returns.  The array keeps the last call's contents (its counters are
+ * cleared on entry), so calls that overlap on the GPU race: serialise them.
+ * Calls after cudaDeviceReset are not supported.  KQ_WARN_PCG_MAXIT if the
+ * tolerance was not met; errors are reported by kq_global_error(). */
 kq_status kkt_pcg_solve_static(int64_t n, int64_t m, const double *H, const double *A,
                                const double *Dl, const double *Du, const double *dg,
                                const double *rhs, double *sol, double tol, int maxit,
                                void *stream, int *iters, double *rel_res);
+
+/* kq_barrier_selftest: self-test of the bounded device waits that every
+ * persistent kernel relies on (section 3.2's PCG runs as one cooperative
+ * launch with grid barriers; no paper counterpart).  Launches `ctas` CTAs
+ * that each enter the library's grid barrier once with an arrival target one
+ * above the CTAs launched, so the barrier cannot complete; each CTA gives up
+ * after budget_s seconds (0 < budget_s <= 5) and records KQ_ERR_TIMEOUT.
+ * Returns KQ_ERR_TIMEOUT (expected), *gave_up = CTAs that gave up,
+ * *elapsed_ms = device time of the launch.  The CUDA context stays usable.
+ * Synchronises the device; allocates four words (freed before return). */
+kq_status kq_barrier_selftest(int ctas, double budget_s, int *gave_up, double *elapsed_ms);
 
 /* Library-wide: message of the last failure of a call that had no handle
  * (qp_create). */

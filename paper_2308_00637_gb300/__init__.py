@@ -28,7 +28,7 @@ STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_
                 5: "WARN_PCG_MAXIT", 6: "ERR_IPM_MAXIT", 7: "ERR_TIMEOUT", 8: "ERR_NUMERIC",
                 9: "ERR_STATE"}
 KQ_H_DENSE, KQ_H_CSR_LSQ, KQ_H_LOWRANK = 0, 1, 2
-KQ_A_NONE, KQ_A_DENSE, KQ_A_ROWS_OF_P = 0, 1, 3
+KQ_A_NONE, KQ_A_DENSE, KQ_A_CSR, KQ_A_ROWS_OF_P = 0, 1, 2, 3
 KQ_F64, KQ_F32, KQ_BF16 = 0, 1, 2
 KQ_PREC_F64, KQ_PREC_MIXED = 0, 1
 
@@ -41,7 +41,8 @@ class KqHop(C.Structure):
 
 class KqAmat(C.Structure):
     _fields_ = [("kind", C.c_int), ("dtype", C.c_int), ("m", C.c_int64), ("val", C.c_void_p),
-                ("rows", C.c_void_p)]
+                ("rows", C.c_void_p), ("nnz", C.c_int64), ("col", C.c_void_p),
+                ("rowptr", C.c_void_p)]
 
 
 class KqIpmOpts(C.Structure):
@@ -117,6 +118,7 @@ def load(path: str = LIB_PATH):
         "kq_global_error": (C.c_char_p, []),
         "kkt_pcg_solve_static": (I, [I64, I64, P, P, P, P, P, P, P, D, I, P, C.POINTER(C.c_int),
                                      C.POINTER(D)]),
+        "kq_barrier_selftest": (I, [I, D, C.POINTER(I), C.POINTER(D)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -255,18 +257,44 @@ def qp_residuals(h: Handle, **bufs):
     return norm.value
 
 
+def _dev_ptr(a, name):
+    """Device pointer of a contiguous CUDA tensor (None passes as NULL); the
+    allocation-free entry point takes device memory only, so host arrays are
+    refused here rather than handed to its kernels."""
+    if a is None:
+        return None
+    if not (hasattr(a, "is_cuda") and a.is_cuda):
+        raise TypeError(f"{name} must be a CUDA tensor")
+    return _ptr(a)
+
+
 def kkt_pcg_solve_static(n, m, H, A, Dl, Du, dg, rhs, sol, tol=1e-7, maxit=5000, stream=None,
                          allow=(KQ_OK, KQ_WARN_PCG_MAXIT)):
-    """Allocation-free dense PCG solve (all buffers are device tensors)."""
+    """Allocation-free dense PCG solve; every buffer is a CUDA tensor (float64)."""
     it = C.c_int()
     rel = C.c_double()
     lib = load()
-    rc = lib.kkt_pcg_solve_static(int(n), int(m), _ptr(H), _ptr(A), _ptr(Dl), _ptr(Du), _ptr(dg),
-                                  _ptr(rhs), _ptr(sol), float(tol), int(maxit), stream,
+    n, m = int(n), int(m)
+    if n <= 0 or n > 4096 or m < 0 or m > 4096:
+        rc = lib.kkt_pcg_solve_static(n, m, None, None, None, None, None, None, None, float(tol),
+                                      int(maxit), stream, C.byref(it), C.byref(rel))
+        raise KQError(rc, lib.kq_global_error().decode())
+    ptrs = [_dev_ptr(a, k) for a, k in ((H, "H"), (A, "A"), (Dl, "Dl"), (Du, "Du"), (dg, "dg"),
+                                        (rhs, "rhs"), (sol, "sol"))]
+    rc = lib.kkt_pcg_solve_static(n, m, *ptrs, float(tol), int(maxit), stream,
                                   C.byref(it), C.byref(rel))
     if rc not in allow:
         raise KQError(rc, lib.kq_global_error().decode())
     return rc, it.value, rel.value
+
+
+def barrier_selftest(ctas=4, budget_s=0.05):
+    """Bounded-wait self-test (kq_barrier_selftest): returns (status, CTAs
+    that gave up, device ms).  The expected status is KQ_ERR_TIMEOUT."""
+    gave = C.c_int()
+    ms = C.c_double()
+    rc = load().kq_barrier_selftest(int(ctas), float(budget_s), C.byref(gave), C.byref(ms))
+    return rc, gave.value, ms.value
 
 
 def qp_scaling(h: Handle):
@@ -325,6 +353,15 @@ def create_from(qp, device_tensors: bool = False, stream=None) -> Handle:
         A = KqAmat()
         if qp.akind == "rows_of_p":
             A.kind, A.m, A.rows = KQ_A_ROWS_OF_P, len(qp.a_rows), _ptr(buf(qp.a_rows, np.int32))
+        elif qp.akind == "csr":
+            Ac = qp.A.tocsr()
+            A.kind, A.m, A.nnz = KQ_A_CSR, Ac.shape[0], Ac.nnz
+            if Ac.dtype == np.float32:
+                A.dtype, A.val = KQ_F32, _ptr(buf(Ac.data, np.float32))
+            else:
+                A.dtype, A.val = KQ_F64, _ptr(buf(Ac.data, np.float64))
+            A.col = _ptr(buf(Ac.indices, np.int32))
+            A.rowptr = _ptr(buf(Ac.indptr, np.int64))
         else:
             Am = np.asarray(qp.A)
             A.kind, A.m = KQ_A_DENSE, Am.shape[0]
@@ -458,6 +495,8 @@ def _batch_lib():
         lib.qp_batch_last_error.argtypes = [P]
         lib.kq_batch_error.restype = C.c_char_p
         lib.kq_batch_error.argtypes = []
+        lib.qp_batch_solution.restype = C.c_int
+        lib.qp_batch_solution.argtypes = [P, C.c_int] + [P] * 6
         lib._batch_sigs = True
     return lib
 
@@ -520,6 +559,21 @@ def ipm_solve_batch(batch: Batch, opts: Optional[KqIpmOpts] = None, xs=None,
     if rc not in allow:
         raise KQError(rc, lib.qp_batch_last_error(batch.b).decode())
     return rc, list(status), st
+
+
+def qp_batch_solution(batch: Batch, i: int, qp):
+    """QP i's iterate in original units: dict of host arrays x, lam_lA,
+    lam_uA, lam_lx, lam_ux, lam_e (the layout of ``solve``)."""
+    lib = _batch_lib()
+    n, m, me = qp.n, qp.m, qp.me
+    out = {k: np.zeros(s) for k, s in (("x", n), ("lam_lA", m), ("lam_uA", m), ("lam_lx", n),
+                                       ("lam_ux", n), ("lam_e", me))}
+    rc = lib.qp_batch_solution(batch.b, int(i), *[_ptr(out[k]) for k in
+                                                  ("x", "lam_lA", "lam_uA", "lam_lx", "lam_ux",
+                                                   "lam_e")])
+    if rc != KQ_OK:
+        raise KQError(rc, lib.qp_batch_last_error(batch.b).decode())
+    return out
 
 
 def qp_batch_destroy(batch: Batch):

@@ -199,6 +199,17 @@ kq_status qp_create_batch(kq_batch *out, int nqp, const kq_qp_desc *d, void *str
   return KQ_OK;
 }
 
+kq_status qp_batch_solution(kq_batch b, int i, double *x, double *lam_lA, double *lam_uA,
+                            double *lam_lx, double *lam_ux, double *lam_e) {
+  if (!b) return bfail(nullptr, KQ_ERR_ARG, "null batch");
+  if (i < 0 || i >= (int)b->qps.size()) return bfail(b, KQ_ERR_ARG, "QP index out of range");
+  kq_problem *h = b->qps[i];
+  if (outputs_enqueue(h, x, lam_lA, lam_uA, lam_lx, lam_ux, lam_e) != KQ_OK)
+    return bfail(b, KQ_ERR_CUDA, h->err);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) return bfail(b, KQ_ERR_CUDA, "batch solution copy");
+  return KQ_OK;
+}
+
 kq_status qp_batch_info(kq_batch b, int *nqp, int64_t *n) {
   if (!b) return bfail(nullptr, KQ_ERR_ARG, "null batch");
   if (nqp) *nqp = (int)b->qps.size();

@@ -92,6 +92,20 @@ __global__ void k_rho_rows(int64_t m, const int32_t *rows, const int64_t *rowptr
   }
 }
 
+// 1/||row||_2 of the rows of a CSR A
+template <class AS>
+__global__ void k_rho_acsr(int64_t m, const int64_t *rowptr, const AS *val, double *rho) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t i = w0; i < m; i += W) {
+    double s = 0.0;
+    for (int64_t k = rowptr[i] + lane; k < rowptr[i + 1]; k += 32) { const double v = ld_as_f64(val, k); s += v * v; }
+    s = warp_sum(s);
+    if (lane == 0) rho[i] = s > 0.0 ? 1.0 / sqrt(s) : 1.0;
+  }
+}
+
 __global__ void k_scale_vec(int64_t N, double *v, const double *rho, double sc) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     v[i] *= rho ? rho[i] : sc;
@@ -110,11 +124,14 @@ __global__ void k_scale_rows(int64_t m, int64_t n, double *C, double *b, double 
   for (int64_t j = threadIdx.x; j < n; j += blockDim.x) C[e * n + j] *= rho;
 }
 
+// max |v_i| per block; a NaN or an infinity gives +inf (fmax alone would drop NaN)
 __global__ void k_max_abs(int64_t N, const double *v, double *part) {
   __shared__ double sh[32];
   double mx = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
-    mx = fmax(mx, fabs(v[i]));
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    const double a = fabs(v[i]);
+    mx = (a <= 1.79e308) ? fmax(mx, a) : INFINITY;
+  }
   mx = -block_min(-mx, sh);
   if (threadIdx.x == 0) part[blockIdx.x] = mx;
 }
@@ -204,6 +221,29 @@ __global__ void k_rowdot_prows(DevProb P, const double *v, double *t, double *tC
     if (i < P.m) {
       const int64_t r = P.arows[i];
       for (int64_t k = P.rowptr[r] + lane; k < P.rowptr[r + 1]; k += 32) s += (double)P.val[k] * v[P.col[k]];
+      s = warp_sum(s);
+      if (lane == 0) t[i] = P.rhoA[i] * s;
+    } else {
+      const int64_t e = i - P.m;
+      for (int64_t c = lane; c < P.n; c += 32) s += P.Cd[e * P.n + c] * v[c];
+      s = warp_sum(s);
+      if (lane == 0) tC[e] = s;
+    }
+  }
+}
+
+// t_a = rho_a A_a v for the rows of a CSR A, tC_e = C_e v
+template <class AS>
+__global__ void k_rowdot_acsr(DevProb P, const double *v, double *t, double *tC) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const AS *val = reinterpret_cast<const AS *>(P.aval);
+  for (int64_t i = w0; i < P.m + P.me; i += W) {
+    double s = 0.0;
+    if (i < P.m) {
+      for (int64_t k = P.arowptr[i] + lane; k < P.arowptr[i + 1]; k += 32)
+        s += ld_as_f64(val, k) * v[P.acol[k]];
       s = warp_sum(s);
       if (lane == 0) t[i] = P.rhoA[i] * s;
     } else {
@@ -356,6 +396,27 @@ __global__ void k_rows_scatter_dense(DevProb P, RowCoef cf, double *acc1, double
       s1 += cf.c1[P.m + e] * v; s2 += cf.c2[P.m + e] * v; s3 += cf.c3[P.m + e] * v * v;
     }
     acc1[j] += s1; acc2[j] += s2; acc3[j] += s3;
+  }
+}
+
+// scatter through the rows of a CSR A: acc_k += A' c_k (k = 1, 2), acc3 += (A.^2)' c3
+// (the coefficients already carry the row scale, c3 its square)
+template <class AS>
+__global__ void k_acsr_scatter(DevProb P, RowCoef cf, double *acc1, double *acc2, double *acc3) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const AS *val = reinterpret_cast<const AS *>(P.aval);
+  for (int64_t a = w0; a < P.m; a += W) {
+    const double u1 = cf.c1[a], u2 = cf.c2[a], u3 = cf.c3[a];
+    if (u1 == 0.0 && u2 == 0.0 && u3 == 0.0) continue;
+    for (int64_t k = P.arowptr[a] + lane; k < P.arowptr[a + 1]; k += 32) {
+      const double v = ld_as_f64(val, k);
+      const int c = P.acol[k];
+      atomicAdd(acc1 + c, u1 * v);
+      atomicAdd(acc2 + c, u2 * v);
+      atomicAdd(acc3 + c, u3 * v * v);
+    }
   }
 }
 
@@ -541,7 +602,10 @@ size_t dtype_size(int dt) { return dt == KQ_F64 ? 8 : (dt == KQ_F32 ? 4 : 2); }
 kq_status rowdot(kq_problem *h, const double *v, double *t, double *tC) {
   const DevProb &P = h->P;
   if (P.m + P.me == 0) return KQ_OK;
-  if (P.akind == KQ_A_ROWS_OF_P || (P.akind == KQ_A_NONE && P.hkind == KQ_H_CSR_LSQ))
+  if (P.akind == KQ_A_CSR) {
+    if (P.adtype == KQ_F32) k_rowdot_acsr<float><<<NB, NT, 0, h->stream>>>(P, v, t, tC);
+    else k_rowdot_acsr<double><<<NB, NT, 0, h->stream>>>(P, v, t, tC);
+  } else if (P.akind == KQ_A_ROWS_OF_P || (P.akind == KQ_A_NONE && P.hkind == KQ_H_CSR_LSQ))
     k_rowdot_prows<<<NB, NT, 0, h->stream>>>(P, v, t, tC);
   else if (P.adtype == KQ_F32)
     k_rowdot_dense<float><<<NB, NT, 0, h->stream>>>(P, v, t, tC);
@@ -649,10 +713,18 @@ kq_status assemble_enqueue(kq_problem *h) {
   k_rows_resid<<<NB, NT, 0, h->stream>>>(P, h->S, h->K, h->t, h->tC, cf, h->red + 2 * NB);
   ++h->launches;
   if (P.hkind == KQ_H_CSR_LSQ) {
+    // the rows of P (H x and, for ROWS_OF_P, the dose-limit rows)
     k_csr_scatter<<<NB * 4, NT, 0, h->stream>>>(P, h->yP, cf, h->acc1, h->acc2, h->acc3);
     ++h->launches;
-    if (P.me > 0) return kq_fail(h, KQ_ERR_ARG, "CSR_LSQ with equality rows is not supported");
-  } else if (P.m + P.me > 0) {
+  }
+  if (P.akind == KQ_A_CSR && P.m > 0) {
+    if (P.adtype == KQ_F32) k_acsr_scatter<float><<<NB * 4, NT, 0, h->stream>>>(P, cf, h->acc1, h->acc2, h->acc3);
+    else k_acsr_scatter<double><<<NB * 4, NT, 0, h->stream>>>(P, cf, h->acc1, h->acc2, h->acc3);
+    ++h->launches;
+  }
+  // dense general rows and the equality rows (k_rows_scatter_dense reads A
+  // only when it is dense)
+  if ((P.akind == KQ_A_DENSE && P.m > 0) || P.me > 0) {
     if (P.adtype == KQ_F32) k_rows_scatter_dense<float><<<NB, NT, 0, h->stream>>>(P, cf, h->acc1, h->acc2, h->acc3);
     else k_rows_scatter_dense<double><<<NB, NT, 0, h->stream>>>(P, cf, h->acc1, h->acc2, h->acc3);
     ++h->launches;
@@ -812,16 +884,16 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
   if (m > 0 && (!lA || !uA)) return kq_fail(nullptr, KQ_ERR_ARG, "lA/uA required when A has rows");
   if (me > 0 && (!C || !b)) return kq_fail(nullptr, KQ_ERR_ARG, "C/b required when me > 0");
   if (H->kind == KQ_H_CSR_LSQ) {
-    if (akind != KQ_A_NONE && akind != KQ_A_ROWS_OF_P)
-      return kq_fail(nullptr, KQ_ERR_ARG, "CSR_LSQ H supports A = NONE or ROWS_OF_P");
-    if (me > 0) return kq_fail(nullptr, KQ_ERR_ARG, "CSR_LSQ H with equality rows is not supported");
+    if (akind == KQ_A_DENSE)
+      return kq_fail(nullptr, KQ_ERR_ARG, "CSR_LSQ H supports A = NONE, CSR or ROWS_OF_P");
     if (H->dtype != KQ_F32 || H->cols != n || !H->val || !H->col || !H->rowptr || !H->w)
       return kq_fail(nullptr, KQ_ERR_ARG, "CSR_LSQ needs F32 values, col, rowptr, w and cols == n");
   } else if (H->kind == KQ_H_DENSE) {
     if (akind == KQ_A_ROWS_OF_P) return kq_fail(nullptr, KQ_ERR_ARG, "ROWS_OF_P needs CSR_LSQ H");
     if (!H->val) return kq_fail(nullptr, KQ_ERR_ARG, "dense H values missing");
   } else if (H->kind == KQ_H_LOWRANK) {
-    if (akind != KQ_A_NONE) return kq_fail(nullptr, KQ_ERR_ARG, "LOWRANK H supports A = NONE only");
+    if (akind != KQ_A_NONE && akind != KQ_A_CSR)
+      return kq_fail(nullptr, KQ_ERR_ARG, "LOWRANK H supports A = NONE or CSR");
     if (!H->val || H->rows != n || H->cols <= 0 || H->dtype == KQ_BF16)
       return kq_fail(nullptr, KQ_ERR_ARG, "LOWRANK needs Z (n x k, F32/F64)");
   } else {
@@ -830,6 +902,11 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
   if (akind == KQ_A_DENSE && (!A->val || (A->dtype != KQ_F64 && A->dtype != KQ_F32)))
     return kq_fail(nullptr, KQ_ERR_ARG, "dense A needs F64 or F32 values");
   if (akind == KQ_A_ROWS_OF_P && !A->rows) return kq_fail(nullptr, KQ_ERR_ARG, "ROWS_OF_P needs rows");
+  if (akind == KQ_A_CSR && (A->nnz < 0 || (A->nnz > 0 && (!A->val || !A->col)) || !A->rowptr ||
+                            (A->dtype != KQ_F64 && A->dtype != KQ_F32)))
+    return kq_fail(nullptr, KQ_ERR_ARG, "CSR A needs F64 or F32 values, col, rowptr and nnz >= 0");
+  if (akind != KQ_A_NONE && akind != KQ_A_DENSE && akind != KQ_A_CSR && akind != KQ_A_ROWS_OF_P)
+    return kq_fail(nullptr, KQ_ERR_ARG, "unknown A kind");
 
   kq_problem *h = new kq_problem();
   h->stream = (cudaStream_t)stream;
@@ -837,7 +914,7 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
   DevProb &P = h->P;
   P.n = n; P.m = m; P.me = me; P.nkp = h->nkp;
   P.hkind = H->kind; P.hdtype = H->dtype; P.akind = akind;
-  P.adtype = akind == KQ_A_DENSE ? A->dtype : KQ_F64;
+  P.adtype = (akind == KQ_A_DENSE || akind == KQ_A_CSR) ? A->dtype : KQ_F64;
   auto fail = [&](kq_status st, const std::string &msg) {
     g_global_err = msg;
     qp_destroy(h);
@@ -956,6 +1033,26 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
       return fail(KQ_ERR_CUDA, "A upload");
     if (A->dtype == KQ_F64) k_rho_dense<double><<<NB, NT, 0, s>>>(m, n, P.ald, (const double *)P.Ad, rhoA);
     else k_rho_dense<float><<<NB, NT, 0, s>>>(m, n, P.ald, (const float *)P.Ad, rhoA);
+  } else if (akind == KQ_A_CSR) {
+    const size_t es = dtype_size(A->dtype);
+    const int64_t annz = A->nnz;
+    P.arowptr = (const int64_t *)up(A->rowptr, (m + 1) * sizeof(int64_t));
+    P.acol = (const int32_t *)up(A->col, std::max<int64_t>(annz, 1) * sizeof(int32_t));
+    P.aval = up(A->val, std::max<int64_t>(annz, 1) * es);
+    P.annz = annz;
+    int *bad = dalloc<int>(h, 1);
+    if (!P.arowptr || !P.acol || !P.aval || !bad) return fail(KQ_ERR_OOM, "CSR A");
+    if (annz == 0) {
+      cudaMemsetAsync((void *)P.acol, 0, sizeof(int32_t), s);
+      cudaMemsetAsync((void *)P.aval, 0, es, s);
+    }
+    k_check_csr<<<NB, NT, 0, s>>>(m, n, annz, P.arowptr, P.acol, 0, nullptr, bad);
+    int hbad = 0;
+    cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return fail(KQ_ERR_CUDA, "CSR A check");
+    if (hbad) return fail(KQ_ERR_ARG, "invalid CSR structure of A (rowptr or col out of range)");
+    if (A->dtype == KQ_F64) k_rho_acsr<double><<<NB, NT, 0, s>>>(m, P.arowptr, (const double *)P.aval, rhoA);
+    else k_rho_acsr<float><<<NB, NT, 0, s>>>(m, P.arowptr, (const float *)P.aval, rhoA);
   } else if (akind == KQ_A_ROWS_OF_P) {
     const int32_t *rows = P.arows;   // uploaded and checked with the CSR structure
     k_rho_rows<<<NB, NT, 0, s>>>(m, rows, P.rowptr, P.val, rhoA);

@@ -26,10 +26,15 @@ struct DevProb {
   // LOWRANK: H = Zs Zs', Zs = sqrt(sigma) Z, n x k row-major
   int64_t k = 0;
   const void *Z = nullptr;
-  // dense A (rows already scaled), m x n row-major
+  // general rows, stored unscaled (the row scale rhoA is applied on the fly):
+  // DENSE m x n row-major (leading dimension ald), or CSR (arowptr, acol, aval)
   int akind = 0, adtype = 0;
   const void *Ad = nullptr;
-  const double *rhoA = nullptr;      // m (ROWS_OF_P: applied on the fly)
+  const int64_t *arowptr = nullptr;  // CSR: m + 1
+  const int32_t *acol = nullptr;     // CSR: annz
+  const void *aval = nullptr;        // CSR: annz values (adtype)
+  int64_t annz = 0;
+  const double *rhoA = nullptr;      // m: 1 / ||A_i||_2
   const double *lA = nullptr, *uA = nullptr;   // scaled, m
   const uint8_t *hasl = nullptr, *hasu = nullptr;
   // equality rows (scaled), me x n row-major, and rhs

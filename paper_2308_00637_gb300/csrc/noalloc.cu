@@ -7,6 +7,7 @@
 // buffer, all in device memory.
 #include "common.cuh"
 #include "kq_internal.h"
+#include <atomic>
 #include <cmath>
 #include <string>
 
@@ -30,8 +31,12 @@ constexpr int64_t KQ_STATIC_DOUBLES = 5 * KQ_STATIC_MAX_NKP + 2 * KQ_STATIC_MAX_
 static __device__ __align__(256) double g_kq_static_scratch[KQ_STATIC_DOUBLES];
 
 // Device address of the array, looked up once per device (host code must not
-// use the symbol itself: in host code it is only a stand-in).
-double *g_scratch_addr[64] = {nullptr};
+// use the symbol itself: in host code it is only a stand-in).  Atomic so that
+// host threads calling on different handles or streams read and publish it
+// without a data race; two threads racing on the first call both look it up
+// and store the same value.  Calls after cudaDeviceReset are not supported
+// (the module is reloaded and the cached address is stale).
+std::atomic<double *> g_scratch_addr[64];
 thread_local std::string g_static_err;
 
 // Jacobi diagonal of K (Eq. (9)) for dense H and A with all rows two-sided:
@@ -87,13 +92,15 @@ extern "C" kq_status kkt_pcg_solve_static(int64_t n, int64_t m, const double *H,
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
     return kq_fail(nullptr, KQ_ERR_CUDA, "kkt_pcg_solve_static: no current CUDA device");
   // one-time set-up on this device: the device address of the static array
-  if (!g_scratch_addr[dev]) {
+  double *base = g_scratch_addr[dev].load(std::memory_order_acquire);
+  if (!base) {
     void *p = nullptr;
     const cudaError_t e = cudaGetSymbolAddress(&p, g_kq_static_scratch);
     if (e != cudaSuccess || !p)
       return kq_fail(nullptr, KQ_ERR_CUDA,
                      std::string("kkt_pcg_solve_static: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_addr[dev] = static_cast<double *>(p);
+    base = static_cast<double *>(p);
+    g_scratch_addr[dev].store(base, std::memory_order_release);
   }
   int sms = 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
@@ -101,7 +108,6 @@ extern "C" kq_status kkt_pcg_solve_static(int64_t n, int64_t m, const double *H,
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t nkp = n + 2 * m;
   // carve the static array
-  double *base = g_scratch_addr[dev];
   double *r = base, *y = r + nkp, *pb0 = y + nkp, *pb1 = pb0 + nkp, *diag = pb1 + nkp;
   double *qlam = diag + nkp, *accx = qlam + 2 * m, *rho = accx + n, *cl = rho + m, *cu = cl + m;
   uint8_t *hasl = reinterpret_cast<uint8_t *>(cu + m);   // m bytes

@@ -264,7 +264,9 @@ struct OpDense {
     const AS *Ad = reinterpret_cast<const AS *>(P.Ad);
     const bool hvec = (hld % 8 == 0) && ((reinterpret_cast<uintptr_t>(Hd) & 15) == 0);
     const bool avec = (ald % 8 == 0) && ((reinterpret_cast<uintptr_t>(Ad) & 15) == 0);
-    const bool colpass = n >= 512 && m > 0 && a.coefA != nullptr && avec;
+    // general rows handled here only when A is dense (a CSR A has its own pass)
+    const int64_t md = P.akind == KQ_A_DENSE ? m : 0;
+    const bool colpass = n >= 512 && md > 0 && a.coefA != nullptr && avec;
     double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
     for (int64_t j = tid; j < npad; j += blockDim.x) {
       pw[j] = j < n ? (T)(ldcg(ysrc + j) + beta * ldcg(pold + j)) : (T)0;
@@ -323,9 +325,9 @@ struct OpDense {
     };
     // warps continue the global row numbering after the H rows
     const int64_t a0 = ((gw0 - n) % GW + GW) % GW;   // first A row of this warp
-    for (int64_t ai = a0; ai < m; ai += 2 * GW) {
+    for (int64_t ai = a0; ai < md; ai += 2 * GW) {
       const int64_t a2 = ai + GW;
-      const bool two = a2 < m;
+      const bool two = a2 < md;
       T d0, d1;
       row_dot2<AS, T>(Ad + ai * ald, Ad + (two ? a2 : ai) * ald, two, pw, n, avec, lane, d0, d1);
       arow(ai, d0);
@@ -360,12 +362,12 @@ struct OpDense {
       if (!ok) return 0.0;
       const int64_t nblk = (n + 255) / 256;
       int64_t nrs = (4 * GW + nblk - 1) / nblk;
-      nrs = nrs < 1 ? 1 : (nrs > m ? m : nrs);
-      const int64_t rows_per = (m + nrs - 1) / nrs;
+      nrs = nrs < 1 ? 1 : (nrs > md ? md : nrs);
+      const int64_t rows_per = (md + nrs - 1) / nrs;
       for (int64_t task = gw0; task < nblk * nrs; task += GW) {
         const int64_t blk = task % nblk, rs = task / nblk;
         const int64_t c0 = blk * 256 + 8 * lane;
-        const int64_t a0 = rs * rows_per, a1 = (a0 + rows_per < m) ? a0 + rows_per : m;
+        const int64_t a0 = rs * rows_per, a1 = (a0 + rows_per < md) ? a0 + rows_per : md;
         T s8[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) s8[k] = (T)0;
@@ -442,7 +444,8 @@ struct OpLowrank {
       if (lane == 0) {
         double hz = (double)s;
         for (int64_t e = 0; e < me; ++e) hz += P.Cd[e * n + i] * cf[e];
-        accg[i] = (T)hz;
+        if (P.akind == KQ_A_CSR) atomicAdd(accg + i, (T)hz);   // shared with the A-row scatter
+        else accg[i] = (T)hz;
         pq += ps[i - r0] * hz;
       }
     }
@@ -1255,21 +1258,103 @@ template <> struct IsRows<OpCsrRows> { static constexpr bool value = true; };
 template <class OP> struct IsLowrank { static constexpr bool value = false; };
 template <class ZS> struct IsLowrank<OpLowrank<ZS>> { static constexpr bool value = true; };
 
+// ---------------------------------------------------------------- general rows of a CSR A (any operator)
+// Rows of a CSR A, and (for the CSR least-squares operators, whose passes
+// read only P) the dense equality rows C, one warp per row over the warps of
+// the problem's CTAs: t = rho A_i p_x, coefficient 2 t (1/D_l + 1/D_u) + p_l -
+// p_u scattered into the top block with global atomics (the columns of a
+// general row can be anywhere in [0, n)), bottom entries (t + D_l p_l,
+// -t + D_u p_u) written directly.  Returns this thread's share of p'Kp.
+template <class T, class AS>
+__device__ double csr_a_rows(const PcgArgs &a, const double *ysrc, const double *pold, double beta,
+                             int vcta, int vG) {
+  const DevProb &P = a.P;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int64_t n = P.n, m = P.m, me = P.me;
+  const int64_t lo_off = n + me, up_off = n + me + m;
+  const int64_t gw0 = (int64_t)vcta * nw + warp, GW = (int64_t)vG * nw;
+  T *accg = reinterpret_cast<T *>(a.accx);
+  const AS *val = reinterpret_cast<const AS *>(P.aval);
+  double pq = 0.0;
+  if (P.akind == KQ_A_CSR) {
+    for (int64_t ai = gw0; ai < m; ai += GW) {
+      const bool hl = P.hasl[ai] != 0, hu = P.hasu[ai] != 0;
+      if (!hl && !hu) {
+        if (lane == 0) { a.qlam[me + ai] = 0.0; a.qlam[me + m + ai] = 0.0; }
+        continue;
+      }
+      const int64_t k0 = P.arowptr[ai], k1 = P.arowptr[ai + 1];
+      T dot = (T)0;
+      for (int64_t k = k0 + lane; k < k1; k += 32) {
+        const int c = P.acol[k];
+        dot += (T)ld_as_f64(val, k) * (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+      }
+      dot = warp_sum(dot);
+      const double rho_a = P.rhoA[ai];
+      const double t = rho_a * (double)dot;
+      const double pl = hl ? ldcg(ysrc + lo_off + ai) + beta * ldcg(pold + lo_off + ai) : 0.0;
+      const double pu = hu ? ldcg(ysrc + up_off + ai) + beta * ldcg(pold + up_off + ai) : 0.0;
+      const double coef = 2.0 * t * (a.cl[ai] + a.cu[ai]) + pl - pu;
+      const T cf = (T)(coef * rho_a);
+      for (int64_t k = k0 + lane; k < k1; k += 32) atomicAdd(accg + P.acol[k], cf * (T)ld_as_f64(val, k));
+      if (lane == 0) {
+        const double ql = hl ? t + a.Dl[ai] * pl : 0.0;
+        const double qu = hu ? -t + a.Du[ai] * pu : 0.0;
+        a.qlam[me + ai] = ql;
+        a.qlam[me + m + ai] = qu;
+        pq += coef * t + pl * ql + pu * qu;
+      }
+    }
+  }
+  if (P.hkind == KQ_H_CSR_LSQ) {
+    // equality rows (scaled, dense): t = C_e p_x, coefficient 2 t / mu + p_e
+    for (int64_t e = gw0; e < me; e += GW) {
+      const double *cr = P.Cd + e * n;
+      T dot = (T)0;
+      for (int64_t j = lane; j < n; j += 32) dot += (T)cr[j] * (T)(ldcg(ysrc + j) + beta * ldcg(pold + j));
+      dot = warp_sum(dot);
+      const double t = (double)dot;
+      const double pe = ldcg(ysrc + n + e) + beta * ldcg(pold + n + e);
+      const double coef = 2.0 * t / a.mu + pe;
+      const T cf = (T)coef;
+      for (int64_t j = lane; j < n; j += 32) {
+        const T v = cf * (T)cr[j];
+        if (v != (T)0) atomicAdd(accg + j, v);
+      }
+      if (lane == 0) {
+        const double qe = t + a.mu * pe;
+        a.qlam[e] = qe;
+        pq += coef * t + pe * qe;
+      }
+    }
+  }
+  return pq;
+}
+
+template <class T>
+__device__ __forceinline__ double extra_rows(const PcgArgs &a, const double *ysrc, const double *pold,
+                                             double beta, int vcta, int vG) {
+  if (a.P.akind != KQ_A_CSR && !(a.P.hkind == KQ_H_CSR_LSQ && a.P.me > 0)) return 0.0;
+  if (a.P.adtype == KQ_F32) return csr_a_rows<T, float>(a, ysrc, pold, beta, vcta, vG);
+  return csr_a_rows<T, double>(a, ysrc, pold, beta, vcta, vG);
+}
+
 template <class OP, class T>
 __device__ __forceinline__ double run_phaseA(const PcgArgs &a, const double *ysrc,
                                              const double *pold, double *pnew, double beta,
                                              int64_t vb, int64_t ve, unsigned char *smem,
                                              PipeState &ps, bool &ok, int vcta, int vG) {
+  double pq;
+  ok = true;
   if constexpr (IsLowrank<OP>::value || IsRows<OP>::value) {
-    ok = true;
-    return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ok);
+    pq = OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ok);
   } else if constexpr (IsStaged<OP>::value) {
-    ok = true;
-    return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ps, ok);
+    pq = OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, ps, ok);
   } else {
-    ok = true;
-    return OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, vcta, vG, ok);
+    pq = OP::template phaseA<T>(a, ysrc, pold, pnew, beta, vb, ve, smem, vcta, vG, ok);
   }
+  if (ok) pq += extra_rows<T>(a, ysrc, pold, beta, vcta, vG);
+  return pq;
 }
 
 // The PCG solve (or one product in APPLY mode) of one problem by the CTAs
@@ -1958,6 +2043,58 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
 }
 
 double pcg_last_kernel_ms(const kq_problem *h) { return h->last_kernel_ms; }
+
+// Self-test of the bounded device waits: every CTA enters the production grid
+// barrier once with an arrival target one above the CTAs launched, so the
+// barrier cannot complete; each wait gives up after its budget and records
+// KQ_ERR_TIMEOUT.
+namespace {
+__global__ void k_barrier_selftest(GridBar g, int *done) {
+  const bool ok = grid_sync(g);
+  if (threadIdx.x == 0 && !ok) atomicAdd(done, 1);
+}
+}  // namespace
+
+extern "C" kq_status kq_barrier_selftest(int ctas, double budget_s, int *gave_up,
+                                         double *elapsed_ms) {
+  if (ctas < 1 || ctas > 1024 || !(budget_s > 0.0) || budget_s > 5.0)
+    return kq_fail(nullptr, KQ_ERR_ARG, "kq_barrier_selftest: 1 <= ctas <= 1024, 0 < budget <= 5 s");
+  unsigned int *w = nullptr;
+  if (cudaMalloc(&w, 4 * sizeof(unsigned int)) != cudaSuccess)
+    return kq_fail(nullptr, KQ_ERR_OOM, "kq_barrier_selftest: work words");
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  kq_status st = KQ_OK;
+  int h[2] = {0, 0};
+  float ms = 0.f;
+  GridBar g;
+  g.count = w;
+  g.gen = w + 1;
+  g.err = reinterpret_cast<int *>(w + 2);
+  g.nblocks = (unsigned)ctas + 1u;   // never reached: nothing else arrives
+  g.budget_ns = (uint64_t)(budget_s * 1e9);
+  if (cudaMemset(w, 0, 4 * sizeof(unsigned int)) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    st = kq_fail(nullptr, KQ_ERR_CUDA, "kq_barrier_selftest: set-up");
+  } else {
+    cudaEventRecord(e0);
+    k_barrier_selftest<<<ctas, 128>>>(g, reinterpret_cast<int *>(w + 3));
+    cudaEventRecord(e1);
+    if (cudaGetLastError() != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(h, w + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      st = kq_fail(nullptr, KQ_ERR_CUDA, "kq_barrier_selftest: launch");
+    } else {
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (gave_up) *gave_up = h[1];
+      if (elapsed_ms) *elapsed_ms = ms;
+      st = h[0] == 7 ? KQ_ERR_TIMEOUT : (h[0] == 0 ? KQ_OK : KQ_ERR_CUDA);
+      if (st == KQ_ERR_TIMEOUT) kq_fail(nullptr, st, "grid barrier exceeded its time budget");
+    }
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(w);
+  return st;
+}
 
 // Fill of the register-streamed layout, one warp per row of P.  The row's
 // nonzeros are ranked by (multiplicity of their bank in the row, descending;

@@ -341,3 +341,85 @@ def tiny_qp(n: int, m: int, seed: int, me: int = 0, two_sided: bool = True,
     return QPData(n=n, hkind="dense", p=p, H=H, akind="dense" if m else "none",
                   A=A if m else None, lA=lo if m else None, uA=hi if m else None,
                   C=C, b=b, lx=lx, ux=ux, meta={"seed": seed, "x0": x0})
+
+
+# ---------------------------------------------------------------------------
+# General sparse rows (Eq. (1) with a CSR A): every H structure above can take
+# a general constraint matrix A in CSR and equality rows C.  The rows are
+# drawn around a reference point x_ref that is strictly inside every bound, so
+# that the problem stays strictly feasible:
+#   A: m rows with nnz_row distinct random columns each, values N(0,1) (or
+#      lognormal(0,1), positive, for dose-like rows), float32 or float64;
+#      lA = A x_ref - U(0.1,1) on every row, uA = A x_ref + U(0.1,1) on a
+#      `two_sided` fraction of the rows (+inf on the others);
+#   C: me dense rows N(0,1), b = C x_ref.
+# Draw order: column keys, values, lower margins, upper margins, two-sided
+# mask, C.
+# ---------------------------------------------------------------------------
+def _sparse_rows(rng, m, n, nnz_row, positive, dtype):
+    indptr = np.arange(m + 1, dtype=np.int64) * nnz_row
+    keys = rng.random((m, n))
+    cols = np.sort(np.argpartition(keys, nnz_row - 1, axis=1)[:, :nnz_row], axis=1)
+    vals = rng.lognormal(0.0, 1.0, m * nnz_row) if positive else rng.standard_normal(m * nnz_row)
+    return sp.csr_matrix((vals.astype(dtype), cols.ravel().astype(np.int32), indptr), shape=(m, n))
+
+
+def with_general_rows(qp: QPData, m: int, nnz_row: int, me: int, x_ref: np.ndarray, seed: int,
+                      two_sided: float = 0.5, positive: bool = False,
+                      dtype=np.float64) -> QPData:
+    """Replace qp's constraint rows by [existing rows as CSR; m new sparse rows]
+    (kind 'csr') and its equality rows by me new dense rows."""
+    rng = np.random.default_rng(seed)
+    n = qp.n
+    R = _sparse_rows(rng, m, n, nnz_row, positive, dtype)
+    Rx = R.astype(np.float64) @ x_ref
+    lo = Rx - rng.uniform(0.1, 1.0, m)
+    hi = Rx + rng.uniform(0.1, 1.0, m)
+    hi[rng.random(m) >= two_sided] = INF
+    old = qp.A_matrix() if qp.akind != "none" else None
+    if old is not None and old.shape[0]:
+        A = sp.vstack([sp.csr_matrix(old, dtype=np.float64).astype(dtype), R]).tocsr()
+        lA = np.concatenate([np.asarray(qp.lA, float), lo])
+        uA = np.concatenate([np.asarray(qp.uA, float), hi])
+    else:
+        A, lA, uA = R, lo, hi
+    C = rng.standard_normal((me, n)) if me else None
+    b = C @ x_ref if me else None
+    meta = dict(qp.meta)
+    meta.update({"general_rows_seed": seed, "x_ref": x_ref})
+    return QPData(n=n, hkind=qp.hkind, p=qp.p, H=qp.H, P=qp.P, w=qp.w, Z=qp.Z, akind="csr",
+                  A=A, lA=lA, uA=uA, C=C, b=b, lx=qp.lx, ux=qp.ux, meta=meta)
+
+
+def dense_qp_general(n: int = 120, m: int = 90, nnz_row: int = 7, me: int = 3,
+                     seed: int = 31) -> QPData:
+    """Dense H (as dense_qp) with a sparse general A and equality rows."""
+    base = dense_qp(n, 1, seed=seed)
+    base.akind, base.A, base.lA, base.uA = "none", None, None, None
+    x_ref = np.random.default_rng([seed, 7]).uniform(-0.5, 0.5, n)
+    return with_general_rows(base, m, nnz_row, me, x_ref, seed + 1)
+
+
+def dose_qp_general(rows: int = 6000, cols: int = 600, nnz_row: int = 40, halfwin: int = 60,
+                    ntarget: int = 300, extra: int = 200, extra_nnz: int = 30, me: int = 2,
+                    seed: int = 33) -> QPData:
+    """Dose-shaped least-squares QP whose dose-limit rows are given as a
+    general CSR A (not as rows of P), plus `extra` sparse positive rows with
+    limits around the reference plan, and me equality rows (the setting of
+    the photon case of section 4: general linear constraints besides the
+    objective's dose matrix)."""
+    base = dose_qp(rows, cols, nnz_row, halfwin, ntarget, seed=seed, unit_dose=True)
+    xhat = base.meta["xhat"]
+    return with_general_rows(base, extra, extra_nnz, me, xhat, seed + 1, two_sided=1.0,
+                             positive=True, dtype=np.float32)
+
+
+def svm_qp_general(N: int = 400, dim: int = 12, m: int = 30, nnz_row: int = 25,
+                   seed: int = 35) -> QPData:
+    """Linear SVM dual (lowrank H, y'a = 0, box bounds) with extra sparse
+    general rows around a = 1/2 (which meets y'a = 0 for balanced labels)."""
+    base = svm_qp(N, dim, seed=seed)
+    x_ref = np.full(N, 0.5)
+    q = with_general_rows(base, m, nnz_row, 0, x_ref, seed + 1)
+    q.C, q.b = base.C, base.b
+    return q

@@ -2,7 +2,7 @@
 per lock-step IPM iteration for all active QPs) against the oracle, per QP.
 
 Small batch: every QP checked (objective within 1e-6 relative of the oracle's,
-feasible).  Medium batch (128 QPs, n log-uniform in [64, 1024], H stored as
+KKT_rel <= 1e-6 with the batch's multipliers).  Medium batch (128 QPs, n log-uniform in [64, 1024], H stored as
 bf16, A as f32): all QPs converge; the smallest, the median and the largest QP
 are checked against the oracle's full solve."""
 import numpy as np
@@ -24,16 +24,28 @@ def kq():
     return m
 
 
-def _check_against_oracle(qp, x, tag):
+def _check_solution(kq, b, k, qp, f_ref, compl_ref, tag):
+    """QP k of the batch: x and its multipliers (qp_batch_solution) against
+    the oracle's objective, KKT_rel <= 1e-6 by the oracle's metric code, and
+    complementarity of the oracle's size (the same mu path)."""
+    out = kq.qp_batch_solution(b, k, qp)
+    met = oracle.kkt_metrics(qp, out["x"], out["lam_lA"], out["lam_uA"], out["lam_lx"],
+                             out["lam_ux"], out["lam_e"])
+    f = met["objective"]
+    print(tag, "df %.2e kkt %.2e compl %.2e (oracle %.2e)" % (
+        abs(f - f_ref) / (1 + abs(f_ref)), met["kkt_rel"], met["compl_rel"], compl_ref))
+    assert abs(f - f_ref) <= 1e-6 * (1 + abs(f_ref)), (tag, f, f_ref)
+    assert met["kkt_rel"] <= 1e-6, (tag, met)
+    assert met["compl_rel"] <= 2.0 * compl_ref + 1e-12, (tag, met["compl_rel"], compl_ref)
+    return out
+
+
+def _check_against_oracle(kq, b, k, qp, x, tag):
     res = oracle.ipm_solve(qp)
     assert res.status == "converged"
-    f_ref = qp.objective(res.x)
-    f = qp.objective(x)
-    assert abs(f - f_ref) <= 1e-6 * (1 + abs(f_ref)), (tag, f, f_ref)
-    # feasibility of x in original units (the batch API returns x only)
-    A = qp.A_matrix()
-    viol = max(0.0, float(np.max(qp.lA - A @ x)), float(np.max(np.abs(x)) - 1.0))
-    assert viol <= 1e-6 * (1 + np.max(np.abs(x))), (tag, viol)
+    ref = oracle.kkt_metrics(qp, res.x, *full_multipliers(res.scaled, res.lam, qp))
+    out = _check_solution(kq, b, k, qp, ref["objective"], ref["compl_rel"], tag)
+    assert np.array_equal(out["x"], x)
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["f64", "mixed"])
@@ -46,7 +58,7 @@ def test_small_batch_against_oracle(kq, prec):
     print("batch", st.as_dict())
     assert rc == kq.KQ_OK and all(s == kq.KQ_OK for s in status)
     for k, qp in enumerate(qps):
-        _check_against_oracle(qp, xs[k], k)
+        _check_against_oracle(kq, b, k, qp, xs[k], k)
     kq.qp_batch_destroy(b)
 
 
@@ -76,5 +88,35 @@ def test_medium_batch(kq):
     ns = np.array([qp.n for qp in qps])
     order = np.argsort(ns, kind="stable")
     for k in (int(order[0]), int(order[len(order) // 2]), int(order[-1])):
-        _check_against_oracle(qps[k], xs[k], (k, int(ns[k])))
+        _check_against_oracle(kq, b, k, qps[k], xs[k], (k, int(ns[k])))
+    kq.qp_batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec", [1, 0], ids=["mixed", "f64"])
+def test_c3_largest_against_oracle(kq, prec):
+    """The large end of the 512-QP batch workload: QPs 5, 9, 10, 12 and 26
+    (n = 2850, 3126, 1904, 2264 and 4048, the largest QP of the batch; bf16
+    H, f32 A) solved together, every QP against the oracle's stored solve
+    (tests/golden/make_oracle_results.py): objective within 1e-6 relative,
+    KKT_rel <= 1e-6 with the batch's multipliers, complementarity of the
+    oracle's size."""
+    import json
+    import os
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden",
+                                       "oracle_results.json")))["c3_subset"]
+    sizes = qpgen.batch_sizes(512, 64, 4096)
+    ids = sorted(int(k) for k in gold)
+    qps = [qpgen.batch_qp(k, sizes[k]) for k in ids]
+    assert [q.n for q in qps] == [gold[str(k)]["n"] for k in ids]
+    b = kq.qp_create_batch(qps)
+    xs = [np.zeros(q.n) for q in qps]
+    rc, status, st = kq.ipm_solve_batch(b, kq.default_ipm_opts(precision=prec), xs)
+    print("c3 subset", st.as_dict())
+    assert rc == kq.KQ_OK and all(s_ == kq.KQ_OK for s_ in status)
+    for j, k in enumerate(ids):
+        g = gold[str(k)]
+        assert g["status"] == "converged"
+        out = _check_solution(kq, b, j, qps[j], g["objective"], g["compl_rel"], (k, qps[j].n))
+        dx = np.max(np.abs(out["x"][g["x_idx"]] - np.array(g["x_at_idx"]))) / (1 + g["x_inf"])
+        print("  x distance at sampled indices %.2e" % dx)
     kq.qp_batch_destroy(b)

@@ -31,6 +31,10 @@ PROBLEMS = {
     # register-streamed operator, lengths that need padding), scattered columns
     "csr_short_irregular": lambda: qpgen.irregular_lsq_qp(max_len=128, long_rows=0, seed=13),
     "lowrank": lambda: qpgen.svm_qp(500, 16, seed=9),
+    # general sparse A (CSR) and equality rows with every H structure (Eq. (1))
+    "dense_csrA_eq": lambda: qpgen.dense_qp_general(),
+    "csr_csrA_eq": lambda: qpgen.dose_qp_general(),
+    "lowrank_csrA_eq": lambda: qpgen.svm_qp_general(),
 }
 
 
@@ -215,3 +219,57 @@ def test_backward_before_solve_is_a_state_error(kq):
     with pytest.raises(kq.KQError) as e:
         kq.qp_backward(h, np.ones(10), np.zeros(10))
     assert e.value.status == kq.KQ_ERR_STATE
+
+
+def test_residuals_worked_example(kq):
+    """The library's residual blocks of Eq. (7) and ||r||_2 on the hand-worked
+    example of the oracle pins (values computed by hand from Eq. (3), not by
+    the oracle)."""
+    from tests.test_oracle import WORKED_BLOCKS, WORKED_NORM2, _worked_qp, _worked_state
+    qp = _worked_qp()
+    S = I.scale(qp)
+    h = kq.create_from(qp)
+    set_gpu_state(kq, h, S, _worked_state(), 0.1)
+    n, m, me = 2, 1, 1
+    bufs = {k: np.zeros(n) for k in ("r_H", "r_lx", "r_ux", "r_c3", "r_c4")}
+    bufs.update({k: np.zeros(m) for k in ("r_lA", "r_uA", "r_c1", "r_c2")})
+    bufs["r_e"] = np.zeros(me)
+    norm = kq.qp_residuals(h, **bufs)
+    # the library stores bound blocks at full length n (0 where a bound is absent)
+    assert np.allclose(bufs["r_H"], WORKED_BLOCKS["r_H"], rtol=0, atol=1e-13)
+    assert np.allclose(bufs["r_lx"], WORKED_BLOCKS["r_lx"], rtol=0, atol=1e-13)
+    assert np.allclose(bufs["r_ux"][:1], WORKED_BLOCKS["r_ux"], rtol=0, atol=1e-13)
+    assert np.allclose(bufs["r_c3"], WORKED_BLOCKS["r_c3"], rtol=0, atol=1e-13)
+    assert np.allclose(bufs["r_c4"][:1], WORKED_BLOCKS["r_c4"], rtol=0, atol=1e-13)
+    for k in ("r_lA", "r_uA", "r_c1", "r_c2", "r_e"):
+        assert np.allclose(bufs[k], WORKED_BLOCKS[k], rtol=0, atol=1e-13), k
+    assert norm == pytest.approx(np.sqrt(WORKED_NORM2), rel=1e-13)
+    kq.qp_destroy(h)
+
+
+def test_initial_point_worked_example(kq):
+    """The library's initial iterate (read back after create) equals the
+    hand-worked R6 values of the oracle pin."""
+    from tests.test_oracle import IP_EXPECT, _ip_qp
+    qp = _ip_qp()
+    h = kq.create_from(qp)
+    n, m = 5, 3
+    bufs = {k: np.zeros(n) for k in ("x", "s_lx", "s_ux", "lam_lx", "lam_ux")}
+    bufs.update({k: np.zeros(m) for k in ("s_lA", "s_uA", "lam_lA", "lam_uA")})
+    bufs["lam_e"] = np.zeros(1)
+    mu = kq.qp_get_state(h, **bufs)
+    assert mu == 1.0
+    assert np.allclose(bufs["x"], IP_EXPECT["x"], rtol=0, atol=1e-14)
+    L, U = [0, 1], [1, 2]              # rows with a finite lower / upper bound
+    Lx, Ux = [0, 1, 4], [0, 2, 4]
+    assert np.allclose(bufs["s_lA"][L], IP_EXPECT["s_lA"], rtol=0, atol=1e-13)
+    assert np.allclose(bufs["s_uA"][U], IP_EXPECT["s_uA"], rtol=0, atol=1e-13)
+    assert np.allclose(bufs["s_lx"][Lx], IP_EXPECT["s_lx"], rtol=0, atol=1e-14)
+    assert np.allclose(bufs["s_ux"][Ux], IP_EXPECT["s_ux"], rtol=0, atol=1e-14)
+    assert np.allclose(bufs["lam_lA"][L], 1.0) and np.allclose(bufs["lam_uA"][U], 1.0)
+    assert np.allclose(bufs["lam_lx"][Lx], 1.0) and np.allclose(bufs["lam_ux"][Ux], 1.0)
+    # absent bounds: multiplier 0
+    assert bufs["lam_uA"][0] == 0.0 and bufs["lam_lA"][2] == 0.0
+    assert bufs["lam_lx"][2] == 0.0 and bufs["lam_ux"][1] == 0.0
+    assert np.allclose(bufs["lam_e"], 0.0)
+    kq.qp_destroy(h)

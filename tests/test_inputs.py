@@ -73,3 +73,20 @@ def test_batch_qp_storage_is_exact():
     assert qp.A.dtype == np.float32 and qp.A.shape == (48, 96)
     # the stored bf16 H is the problem solved: rebuilding it twice gives the same matrix
     assert np.array_equal(H, qp.H_dense())
+
+
+@pytest.mark.parametrize("maker", ["dense_qp_general", "dose_qp_general", "svm_qp_general"])
+def test_general_rows_structure(maker):
+    """General sparse rows: CSR A, reference point strictly inside every row
+    bound, variable bound and on the equality rows."""
+    import scipy.sparse as sp
+    qp = getattr(qpgen, maker)()
+    assert qp.akind == "csr" and sp.issparse(qp.A)
+    A = qp.A.tocsr()
+    assert A.shape == (qp.m, qp.n) and A.has_sorted_indices
+    x = qp.meta["x_ref"]
+    Ax = A.astype(np.float64) @ x
+    assert np.all(Ax > qp.lA) and np.all(Ax < qp.uA)
+    assert np.all(x > qp.lx) and np.all(x < qp.ux)
+    if qp.me:
+        assert np.allclose(qp.C @ x, qp.b)
