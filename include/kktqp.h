@@ -59,7 +59,9 @@ enum {
 /* H operator kinds (section 2.2 / section 3.2: H used only through products) */
 enum { KQ_H_DENSE = 0,     /* explicit symmetric n x n, row-major              */
        KQ_H_CSR_LSQ = 1,   /* H = 2 P' diag(w) P, P CSR (rows x n)             */
-       KQ_H_LOWRANK = 2 }; /* H = Z Z', Z dense n x k row-major                */
+       KQ_H_LOWRANK = 2 }; /* H = Z diag(w) Z' + diag(d0), Z dense n x k       */
+                           /* row-major (w, d0 optional: Z Z' by default); the */
+                           /* quasi-Newton form H0 + U W U' of section 2.1     */
 /* constraint-matrix kinds (the general rows l <= A x <= u of Eq. (1)) */
 enum { KQ_A_NONE = 0,      /* no general rows                                   */
        KQ_A_DENSE = 1,     /* m x n row-major                                   */
@@ -81,7 +83,9 @@ typedef struct {
   const void *val;         /* DENSE: H; LOWRANK: Z; CSR_LSQ: P values           */
   const int32_t *col;      /* CSR_LSQ column indices (sorted not required)     */
   const int64_t *rowptr;   /* CSR_LSQ row pointers (rows+1)                    */
-  const double *w;         /* CSR_LSQ row weights (rows), H = 2 P'diag(w)P     */
+  const double *w;         /* CSR_LSQ row weights (rows), H = 2 P'diag(w)P;    */
+                           /* LOWRANK column weights (k, NULL = all 1)        */
+  const double *d0;        /* LOWRANK diagonal H0 (n, NULL = 0)                 */
 } kq_hop;
 
 typedef struct {
@@ -103,7 +107,10 @@ typedef struct {
   int ipm_maxit;           /* Algorithm 1's N (200)                             */
   double pcg_tol;          /* relative unpreconditioned residual (1e-7)         */
   int pcg_maxit;           /* PCG iterations per Newton solve (5000)            */
-  int precision;           /* KQ_PREC_*                                         */
+  int precision;           /* KQ_PREC_*.  MIXED: once a Newton solve needs FP64  */
+                           /* correction iterations and an FP64 product costs   */
+                           /* under twice an FP32 iteration (latency-bound      */
+                           /* problems), the rest of the solve runs in FP64     */
   int refine_steps;        /* MIXED: FP32 correction solves before FP64 (6); the */
                            /* batched solver hands a QP to FP64 earlier once one*/
                            /* of its FP32 solves fails to halve its residual    */
@@ -111,7 +118,34 @@ typedef struct {
   double timeout_s;        /* device barrier budget per wait (seconds)         */
   int grid_ctas;           /* 0 = auto; else persistent-kernel grid size        */
   int verbose;             /* 1 = one line per IPM iteration on stderr          */
+  int record;              /* 1 = keep one kq_ipm_iter per IPM iteration        */
+                           /*     (qp_iteration_log); default 0                 */
 } kq_ipm_opts;
+
+/* One IPM iteration's record (opts.record = 1): the quantities the paper
+ * follows per iteration -- CG iterations per Newton solve (section 5.1), the
+ * primal, dual and complementarity infeasibilities (section 5.2) and the
+ * conditioning of the Jacobi-preconditioned doubly augmented system (section
+ * 5.3).  lanczos_min / lanczos_max are the extreme eigenvalues of the
+ * Lanczos tridiagonal matrix built from the first PCG pass's alpha and beta
+ * coefficients: Ritz values, so they lie inside the spectrum of
+ * diag(K)^-1/2 K diag(K)^-1/2 and kappa_jacobi = max/min is a lower bound of
+ * its condition number that tightens as the pass runs longer.  diag_ratio =
+ * max diag(K) / min diag(K) is a lower bound of the condition number of the
+ * unpreconditioned K.  Infeasibilities in scaled units, after the step. */
+typedef struct {
+  int it;
+  int pcg_iters;           /* all passes of the Newton solve                    */
+  int pcg_iters_f64;
+  int lanczos_steps;       /* coefficients used (first pass, at most 5000)      */
+  double mu;               /* barrier parameter of the Newton solve             */
+  double res_norm;         /* ||r||_2 after the step (before any mu update)     */
+  double primal_inf, dual_inf, compl_inf;
+  double alpha_x, alpha_lam;
+  double pcg_rel_res;      /* true relative residual of the Newton solve        */
+  double pcg_ms;           /* device time of its persistent launches            */
+  double lanczos_min, lanczos_max, kappa_jacobi, diag_ratio;
+} kq_ipm_iter;
 
 typedef struct {
   int status;              /* final kq_status                                   */
@@ -131,6 +165,8 @@ typedef struct {
   long long pcg_products_f64;  /* products inside FP64 launches (passes + residuals) */
   double pcg_kernel_ms_f64;    /* device time of the FP64 persistent launches       */
   long long pcg_launches_f64;  /* FP64 persistent launches (passes + residuals)     */
+  int switched_to_f64;     /* MIXED: IPM iteration after which the solve ran in   */
+                           /* FP64 (0 = never; see kq_ipm_opts.precision)         */
 } kq_ipm_stats;
 
 typedef struct {
@@ -151,6 +187,7 @@ typedef struct {
   int products_f64;        /* products inside FP64 launches (passes + residuals)*/
   double kernel_ms_f64;    /* device time of the FP64 persistent launches       */
   int launches_f64;        /* FP64 persistent launches (passes + residuals)     */
+  int products;            /* K*v products inside the persistent kernels        */
 } kq_pcg_stats;
 
 /* Fill *o with the paper's settings (gamma 0.99, mu/10, mu_tol 1e-6, PCG tol
@@ -177,6 +214,17 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
                     int64_t me, const double *C, const double *b,
                     const double *lx, const double *ux, void *stream);
 
+/* qp_update: replace the data that a differentiable QP layer varies -- the
+ * linear term p (n), the row bounds lA, uA (m) and the equality right-hand
+ * side b (me) -- keeping H, A, C, the variable bounds and every device
+ * structure built at qp_create.  Any pointer may be NULL (kept); host or
+ * device memory; unscaled values.  The scaling rule of qp_create is applied
+ * again (sigma from the new |p|_inf).  The next ipm_solve starts from the
+ * initial point.  Synchronises the handle's stream.  KQ_ERR_NUMERIC for NaN or
+ * Inf in p. */
+kq_status qp_update(kq_handle h, const double *p, const double *lA, const double *uA,
+                    const double *b);
+
 /* ipm_solve: Algorithm 1 from the initial point (or from the state set by
  * qp_set_state).  Outputs (any may be NULL), original units:
  *  x (n); lam_lA, lam_uA (m, zero where the bound is absent); lam_lx, lam_ux
@@ -185,6 +233,12 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
 kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x,
                     double *lam_lA, double *lam_uA, double *lam_lx,
                     double *lam_ux, double *lam_e, kq_ipm_stats *stats);
+
+/* qp_iteration_log: the records of the last ipm_solve run with
+ * opts.record = 1 (see kq_ipm_iter).  Copies min(cap, count) records to out
+ * (host memory); *count = records available.  KQ_ERR_STATE if no recorded
+ * solve ran. */
+kq_status qp_iteration_log(kq_handle h, kq_ipm_iter *out, int cap, int *count);
 
 /* kkt_pcg_solve: Jacobi-PCG on the K of Eq. (9) at the current iterate and
  * barrier parameter, scaled units, padded layout (NKP = n + me + 2m).
@@ -297,7 +351,7 @@ void qp_batch_destroy(kq_batch b);
  * pre-reserved memory budget; an allocator that must not be bypassed).  The
  * paper has no counterpart; this is a packaging of the library's dense PCG
  * kernel.  It allocates nothing: its work space is one static device array of
- * about 0.78 MB that every GPU loading the library holds until the process
+ * about 0.76 MB that every GPU loading the library holds until the process
  * exits, shared by all calls.
  *  n, m      0 < n <= 4096, 0 <= m <= 4096; larger sizes return KQ_ERR_ARG
  *  H         n x n symmetric (row-major, FP64, device), already scaled

@@ -62,6 +62,8 @@ class Scaled:
     P: Optional[sp.csr_matrix] = None       # csr_lsq: float64 P
     w2: Optional[np.ndarray] = None         # csr_lsq: 2*sigma*w  (H = P' diag(w2) P)
     Z: Optional[np.ndarray] = None          # lowrank: sqrt(sigma) Z (float64)
+    zw: Optional[np.ndarray] = None         # lowrank: column weights W (H = Z W Z' + H0)
+    d0: Optional[np.ndarray] = None         # lowrank: sigma * diagonal H0
     A: object = None                        # scaled rows: dense ndarray or csr
     rhoA: Optional[np.ndarray] = None
     lA: Optional[np.ndarray] = None
@@ -95,14 +97,14 @@ class Scaled:
             return self.H @ v
         if self.hkind == "csr_lsq":
             return self.P.T @ (self.w2 * (self.P @ v))
-        return self.Z @ (self.Z.T @ v)
+        return self.Z @ (self.zw * (self.Z.T @ v)) + self.d0 * v
 
     def Hdiag(self):
         if self.hkind == "dense":
             return np.diag(self.H).copy()
         if self.hkind == "csr_lsq":
             return np.asarray(self.P.multiply(self.P).T @ self.w2).ravel()
-        return np.einsum("ij,ij->i", self.Z, self.Z)
+        return np.einsum("ij,ij,j->i", self.Z, self.Z, self.zw) + self.d0
 
     def Hmat(self):
         """Explicit scaled H (dense) for small problems."""
@@ -110,7 +112,7 @@ class Scaled:
             return self.H
         if self.hkind == "csr_lsq":
             return np.asarray((self.P.T @ sp.diags(self.w2) @ self.P).todense())
-        return self.Z @ self.Z.T
+        return (self.Z * self.zw) @ self.Z.T + np.diag(self.d0)
 
     def Adense(self):
         return self.A.toarray() if sp.issparse(self.A) else np.asarray(self.A)
@@ -136,7 +138,9 @@ def scale(qp) -> Scaled:
         hmax = float(np.max(2.0 * (P.multiply(P).T @ qp.w)))
     else:
         Z = qp.Z.astype(np.float64)
-        hmax = float(np.max(np.einsum("ij,ij->i", Z, Z)))
+        zw = np.ones(Z.shape[1]) if qp.zw is None else np.asarray(qp.zw, float)
+        d0 = np.zeros(n) if qp.d0 is None else np.asarray(qp.d0, float)
+        hmax = float(np.max(np.einsum("ij,ij,j->i", Z, Z, zw) + d0))
     pinf = float(np.max(np.abs(qp.p))) if n else 0.0
     sigma = 1.0 / max(1.0, hmax, pinf)
     S = Scaled(n=n, hkind=qp.hkind, sigma=sigma, p=sigma * np.asarray(qp.p, float))
@@ -147,6 +151,8 @@ def scale(qp) -> Scaled:
         S.w2 = 2.0 * sigma * np.asarray(qp.w, float)
     else:
         S.Z = np.sqrt(sigma) * Z
+        S.zw = zw
+        S.d0 = sigma * d0
     # general rows
     A = qp.A_matrix()
     if sp.issparse(A):
@@ -331,6 +337,14 @@ def jacobi_diagonal(S: Scaled, dg, D):
     return np.concatenate([dx, D])
 
 
+def jacobi_scaled_eigenvalues(K):
+    """Eigenvalues (ascending) of diag(K)^-1/2 K diag(K)^-1/2: the operator
+    Jacobi-preconditioned CG works with, whose condition number section 5.3
+    reports next to that of K itself."""
+    d = 1.0 / np.sqrt(np.diag(K))
+    return np.linalg.eigvalsh(K * d[:, None] * d[None, :])
+
+
 def full_newton_matrix(S: Scaled, st: State, mu: float):
     """Explicit Eq. (7) in the unknown order (dx, dlam_lA, dlam_uA, dlam_lx,
     dlam_ux, dlam_e, ds_lA, ds_uA, ds_lx, ds_ux) with the -C' reading; the
@@ -448,10 +462,13 @@ def newton_direct(S: Scaled, dg, D, r1, r2, solver: str = "auto"):
             ab = _banded_upper(Msp, u)
             dx = sla.solveh_banded(ab, rhs, lower=False)
     elif solver == "schur_woodbury":
-        # Q + B'D^-1B = diag(dg) + Z Z' + C' D_e^-1 C  (no general rows)
-        assert S.hkind == "lowrank" and S.m == 0
-        U = np.hstack([S.Z, (S.C / np.sqrt(D[:S.me, None])).T])
-        Dinv = 1.0 / dg
+        # Q + B'D^-1B = diag(dg + H0) + Z W Z' + B' D^-1 B with B = [C; A_L;
+        # -A_U]: a diagonal plus U U', U = [Z W^1/2, (D^-1/2 B)'] (positive
+        # weights W); capacitance matrix of size k + rows of B
+        assert S.hkind == "lowrank" and np.all(S.zw > 0)
+        B = B_matrix(S)
+        U = np.hstack([S.Z * np.sqrt(S.zw), (B / np.sqrt(D)[:, None]).T])
+        Dinv = 1.0 / (dg + S.d0)
         cap = np.eye(U.shape[1]) + U.T @ (U * Dinv[:, None])
         t = U.T @ (Dinv * rhs)
         dx = Dinv * rhs - Dinv * (U @ sla.solve(cap, t, assume_a="pos"))

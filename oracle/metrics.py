@@ -43,7 +43,9 @@ def _Hx(qp, x):
         P = qp.P.astype(np.float64)
         return 2.0 * (P.T @ (qp.w * (P @ x)))
     Z = qp.Z.astype(np.float64)
-    return Z @ (Z.T @ x)
+    zw = np.ones(Z.shape[1]) if qp.zw is None else np.asarray(qp.zw, float)
+    d0 = np.zeros(qp.n) if qp.d0 is None else np.asarray(qp.d0, float)
+    return Z @ (zw * (Z.T @ x)) + d0 * x
 
 
 def kkt_metrics(qp, x, lam_lA, lam_uA, lam_lx, lam_ux, lam_e):

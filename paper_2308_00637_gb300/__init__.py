@@ -36,7 +36,7 @@ KQ_PREC_F64, KQ_PREC_MIXED = 0, 1
 class KqHop(C.Structure):
     _fields_ = [("kind", C.c_int), ("dtype", C.c_int), ("rows", C.c_int64), ("cols", C.c_int64),
                 ("nnz", C.c_int64), ("val", C.c_void_p), ("col", C.c_void_p),
-                ("rowptr", C.c_void_p), ("w", C.c_void_p)]
+                ("rowptr", C.c_void_p), ("w", C.c_void_p), ("d0", C.c_void_p)]
 
 
 class KqAmat(C.Structure):
@@ -49,7 +49,20 @@ class KqIpmOpts(C.Structure):
     _fields_ = [("gamma", C.c_double), ("mu0", C.c_double), ("mu_tol", C.c_double),
                 ("ipm_maxit", C.c_int), ("pcg_tol", C.c_double), ("pcg_maxit", C.c_int),
                 ("precision", C.c_int), ("refine_steps", C.c_int), ("inner_tol", C.c_double),
-                ("timeout_s", C.c_double), ("grid_ctas", C.c_int), ("verbose", C.c_int)]
+                ("timeout_s", C.c_double), ("grid_ctas", C.c_int), ("verbose", C.c_int),
+                ("record", C.c_int)]
+
+
+class KqIpmIter(C.Structure):
+    _fields_ = [("it", C.c_int), ("pcg_iters", C.c_int), ("pcg_iters_f64", C.c_int),
+                ("lanczos_steps", C.c_int), ("mu", C.c_double), ("res_norm", C.c_double),
+                ("primal_inf", C.c_double), ("dual_inf", C.c_double), ("compl_inf", C.c_double),
+                ("alpha_x", C.c_double), ("alpha_lam", C.c_double), ("pcg_rel_res", C.c_double),
+                ("pcg_ms", C.c_double), ("lanczos_min", C.c_double), ("lanczos_max", C.c_double),
+                ("kappa_jacobi", C.c_double), ("diag_ratio", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class KqIpmStats(C.Structure):
@@ -60,7 +73,8 @@ class KqIpmStats(C.Structure):
                 ("pcg_kernel_ms", C.c_double), ("pcg_launches", C.c_longlong),
                 ("pcg_products", C.c_longlong), ("kernel_launches", C.c_longlong),
                 ("pcg_iters_f64", C.c_longlong), ("pcg_products_f64", C.c_longlong),
-                ("pcg_kernel_ms_f64", C.c_double), ("pcg_launches_f64", C.c_longlong)]
+                ("pcg_kernel_ms_f64", C.c_double), ("pcg_launches_f64", C.c_longlong),
+                ("switched_to_f64", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -75,7 +89,7 @@ class KqPcgStats(C.Structure):
     _fields_ = [("status", C.c_int), ("iters", C.c_int), ("passes", C.c_int),
                 ("rel_res", C.c_double), ("kernel_ms", C.c_double), ("iters_f64", C.c_int),
                 ("products_f64", C.c_int), ("kernel_ms_f64", C.c_double),
-                ("launches_f64", C.c_int)]
+                ("launches_f64", C.c_int), ("products", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -119,6 +133,8 @@ def load(path: str = LIB_PATH):
         "kkt_pcg_solve_static": (I, [I64, I64, P, P, P, P, P, P, P, D, I, P, C.POINTER(C.c_int),
                                      C.POINTER(D)]),
         "kq_barrier_selftest": (I, [I, D, C.POINTER(I), C.POINTER(D)]),
+        "qp_update": (I, [P, P, P, P, P]),
+        "qp_iteration_log": (I, [P, C.POINTER(KqIpmIter), I, C.POINTER(I)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -196,6 +212,22 @@ def qp_create(n, H: KqHop, p, A: Optional[KqAmat] = None, lA=None, uA=None, me=0
     n_, m_, me_, nkp_ = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
     lib.qp_sizes(h, C.byref(n_), C.byref(m_), C.byref(me_), C.byref(nkp_))
     return Handle(h, n_.value, m_.value, me_.value, nkp_.value)
+
+
+def qp_iteration_log(h: Handle):
+    """Per-IPM-iteration records of the last ipm_solve run with record=1, as
+    a list of dicts (see kq_ipm_iter in kktqp.h)."""
+    lib = load()
+    cnt = C.c_int()
+    h.check(lib.qp_iteration_log(h.h, None, 0, C.byref(cnt)))
+    buf = (KqIpmIter * max(1, cnt.value))()
+    h.check(lib.qp_iteration_log(h.h, buf, cnt.value, C.byref(cnt)))
+    return [buf[i].as_dict() for i in range(cnt.value)]
+
+
+def qp_update(h: Handle, p=None, lA=None, uA=None, b=None):
+    """Replace p, lA, uA and/or b (None keeps a value); see qp_update in kktqp.h."""
+    h.check(load().qp_update(h.h, _ptr(p), _ptr(lA), _ptr(uA), _ptr(b)))
 
 
 def qp_destroy(h: Handle):
@@ -347,6 +379,10 @@ def create_from(qp, device_tensors: bool = False, stream=None) -> Handle:
     else:
         H.kind, H.dtype, H.rows, H.cols = KQ_H_LOWRANK, KQ_F32, n, qp.Z.shape[1]
         H.val = _ptr(buf(qp.Z, np.float32))
+        if getattr(qp, "zw", None) is not None:
+            H.w = _ptr(buf(qp.zw, np.float64))
+        if getattr(qp, "d0", None) is not None:
+            H.d0 = _ptr(buf(qp.d0, np.float64))
     A = None
     lA = uA = None
     if qp.akind != "none":
@@ -381,48 +417,82 @@ def create_from(qp, device_tensors: bool = False, stream=None) -> Handle:
     return h
 
 
+class _HandlePool:
+    """Handles of one problem structure (H, A, C, variable bounds), created
+    once and reused: a forward takes a free handle (creating one only when all
+    are in use, e.g. several forwards before their backwards), replaces p, lA,
+    uA and b with qp_update, and keeps the handle until its backward has run
+    (the converged K lives in it)."""
+
+    def __init__(self, qp):
+        self.qp = qp
+        self.free = []
+        self.created = 0
+
+    def take(self):
+        if self.free:
+            return self.free.pop()
+        self.created += 1
+        return create_from(self.qp)
+
+    def give(self, h):
+        self.free.append(h)
+
+
+_POOLS = {}
+
+
+def _pool(qp):
+    key = id(qp)
+    pl = _POOLS.get(key)
+    if pl is None or pl.qp is not qp:
+        pl = _POOLS[key] = _HandlePool(qp)
+    return pl
+
+
 def _qp_torch_layer():
     """Build the torch.autograd.Function lazily (torch is optional for the
     plain C-ABI binding)."""
     import torch
 
+    def _dev(t, n):
+        if n == 0 or t is None:
+            return None
+        return t.detach().to(dtype=torch.float64).contiguous()
+
     class QPFunction(torch.autograd.Function):
         """x* = argmin of the QP with linear term p, row bounds lA/uA and
         equality right-hand side b (the structure H, A, C and the variable
-        bounds come from ``qp``).  Forward: qp_create + ipm_solve on the GPU.
+        bounds come from ``qp``).  Forward: qp_update + ipm_solve on a pooled
+        handle (the tensors are passed as device pointers, no host copy).
         Backward: qp_backward, one PCG solve with the converged KKT matrix
         (Eq. (9)); gradients in original units, zero for absent bounds."""
 
         @staticmethod
         def forward(ctx, p, lA, uA, b, qp, opts):
-            import copy
-            q2 = copy.copy(qp)
-            q2.p = p.detach().double().cpu().numpy()
-            if qp.akind != "none":
-                q2.lA = lA.detach().double().cpu().numpy()
-                q2.uA = uA.detach().double().cpu().numpy()
-            if qp.C is not None and qp.C.shape[0]:
-                q2.b = b.detach().double().cpu().numpy()
-            h = create_from(q2)
+            pool = _pool(qp)
+            h = pool.take()
+            pt, lt, ut, bt = _dev(p, h.n), _dev(lA, h.m), _dev(uA, h.m), _dev(b, h.me)
+            torch.cuda.current_stream().synchronize()
+            qp_update(h, pt, lt, ut, bt)
             x = torch.zeros(h.n, dtype=torch.float64, device=p.device)
             ipm_solve(h, opts, x=x)
-            ctx.h = h
-            ctx.devices = p.device
+            ctx.h, ctx.pool, ctx.dev = h, pool, p.device
             return x
 
         @staticmethod
         def backward(ctx, gx):
-            h = ctx.h
-            dev = ctx.devices
-            g = gx.detach().double().contiguous()
+            h, dev = ctx.h, ctx.dev
+            g = gx.detach().double().contiguous().to(dev)
             gp = torch.zeros(h.n, dtype=torch.float64, device=dev)
             glA = torch.zeros(h.m, dtype=torch.float64, device=dev)
             guA = torch.zeros(h.m, dtype=torch.float64, device=dev)
             gb = torch.zeros(h.me, dtype=torch.float64, device=dev)
-            qp_backward(h, g.to(dev), gp, glA if h.m else None, guA if h.m else None,
+            torch.cuda.current_stream().synchronize()
+            qp_backward(h, g, gp, glA if h.m else None, guA if h.m else None,
                         gb if h.me else None)
-            torch.cuda.synchronize()
-            qp_destroy(h)
+            ctx.pool.give(h)
+            ctx.h = None
             return gp, glA, guA, gb, None, None
 
     return QPFunction
@@ -432,7 +502,9 @@ _QPF = None
 
 
 def qp_layer(qp, p, lA, uA, b, opts: Optional[KqIpmOpts] = None):
-    """Differentiable QP solution x*(p, lA, uA, b) (torch tensors on cuda)."""
+    """Differentiable QP solution x*(p, lA, uA, b) (torch tensors on cuda).
+    The structure (H, A, C, variable bounds) is taken from ``qp``; its device
+    handles are built once per ``qp`` object and reused across calls."""
     global _QPF
     if _QPF is None:
         _QPF = _qp_torch_layer()

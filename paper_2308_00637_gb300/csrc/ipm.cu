@@ -12,6 +12,7 @@
 #include "common.cuh"
 #include "kq_internal.h"
 #include <chrono>
+#include <cstdlib>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -30,22 +31,52 @@ __global__ void k_flags(int64_t N, const double *lo, const double *hi, uint8_t *
   }
 }
 
+// per-block min of v and min of -v (max) into part[b], part[NB + b]
+__global__ void k_minmax(int64_t N, const double *v, double *part) {
+  __shared__ double sh[32];
+  double mn = INFINITY, mx = INFINITY;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    mn = fmin(mn, v[i]);
+    mx = fmin(mx, -v[i]);
+  }
+  mn = block_min(mn, sh);
+  mx = block_min(mx, sh);
+  if (threadIdx.x == 0) { part[blockIdx.x] = mn; part[NB + blockIdx.x] = mx; }
+}
+
+// qp_update: bounds replaced by unscaled values (new_l / new_u) are divided
+// by their row norms; flags are recomputed from finiteness (scaling keeps it)
+__global__ void k_flags_scaled(int64_t m, double *lA, double *uA, bool new_l, bool new_u,
+                               const double *rho, uint8_t *hl, uint8_t *hu) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
+    if (new_l) lA[i] *= rho[i];
+    if (new_u) uA[i] *= rho[i];
+    hl[i] = isfinite(lA[i]) ? 1 : 0;
+    hu[i] = isfinite(uA[i]) ? 1 : 0;
+  }
+}
+
 template <class HS>
 __global__ void k_dense_diag(int64_t n, int64_t ld, const HS *H, double *d) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     d[i] = ld_as_f64(H, i * ld + i);
 }
 
+// diag(Z diag(zw) Z' + diag(d0))_i = sum_c zw_c Z_ic^2 + d0_i (zw, d0 optional)
 template <class ZS>
-__global__ void k_rownorm2(int64_t rows, int64_t k, const ZS *Z, double *d) {
+__global__ void k_rownorm2(int64_t rows, int64_t k, const ZS *Z, const double *zw,
+                           const double *d0, double *d) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
   for (int64_t i = w0; i < rows; i += W) {
     double s = 0.0;
-    for (int64_t c = lane; c < k; c += 32) { const double v = ld_as_f64(Z, i * k + c); s += v * v; }
+    for (int64_t c = lane; c < k; c += 32) {
+      const double v = ld_as_f64(Z, i * k + c);
+      s += (zw ? zw[c] : 1.0) * v * v;
+    }
     s = warp_sum(s);
-    if (lane == 0) d[i] = s;
+    if (lane == 0) d[i] = s + (d0 ? d0[i] : 0.0);
   }
 }
 
@@ -296,17 +327,18 @@ __global__ void k_zt(DevProb P, const double *v, double *g) {
   }
 }
 
+// hx = sigma (Z diag(zw) g + d0 v)
 template <class ZS>
-__global__ void k_zg(DevProb P, const double *g, double *hx) {
+__global__ void k_zg(DevProb P, const double *g, const double *v, double *hx) {
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const ZS *Z = reinterpret_cast<const ZS *>(P.Z);
   for (int64_t i = w0; i < P.n; i += W) {
     double s = 0.0;
-    for (int64_t c = lane; c < P.k; c += 32) s += ld_as_f64(Z, i * P.k + c) * g[c];
+    for (int64_t c = lane; c < P.k; c += 32) s += ld_as_f64(Z, i * P.k + c) * g[c] * (P.zw ? P.zw[c] : 1.0);
     s = warp_sum(s);
-    if (lane == 0) hx[i] = P.hscale * s;
+    if (lane == 0) hx[i] = P.hscale * (s + (P.d0 ? P.d0[i] * v[i] : 0.0));
   }
 }
 
@@ -324,9 +356,9 @@ struct RowCoef { double *c1, *c2, *c3; };
 
 __global__ void k_rows_resid(DevProb P, DevState S, DevKKT K, const double *t, const double *tC,
                              RowCoef cf, double *part) {
-  __shared__ double sh[32];
+  __shared__ double sh[32 * 2];
   const double mu = K.mu;
-  double ss[1] = {0.0};
+  double ss[2] = {0.0, 0.0};   // [primal (row and equality residuals), complementarity]
   const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < P.m; a += (int64_t)gridDim.x * blockDim.x) {
     const bool hl = P.hasl[a], hu = P.hasu[a];
@@ -362,7 +394,8 @@ __global__ void k_rows_resid(DevProb P, DevState S, DevKKT K, const double *t, c
     K.rhs[up_off + a] = r2u;
     K.diag[lo_off + a] = Dl;
     K.diag[up_off + a] = Du;
-    ss[0] += rl * rl + ru * ru + r1 * r1 + r2 * r2;
+    ss[0] += rl * rl + ru * ru;
+    ss[1] += r1 * r1 + r2 * r2;
   }
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < P.me; e += (int64_t)gridDim.x * blockDim.x) {
     const double re = tC[e] - P.b[e] + mu * S.le[e];
@@ -374,8 +407,8 @@ __global__ void k_rows_resid(DevProb P, DevState S, DevKKT K, const double *t, c
     K.diag[P.n + e] = mu;
     ss[0] += re * re;
   }
-  block_sum<1>(ss, sh);
-  if (threadIdx.x == 0) part[blockIdx.x] = ss[0];
+  block_sum<2>(ss, sh);
+  if (threadIdx.x == 0) { part[blockIdx.x] = ss[0]; part[NB + blockIdx.x] = ss[1]; }
 }
 
 // scatter for dense rows (general rows of a dense A and the equality rows):
@@ -442,9 +475,9 @@ __global__ void k_csr_scatter(DevProb P, const double *y, RowCoef cf, double *ac
 // x part: r_H, bound residuals, r1, rhs_x = r1 + acc2, diag_x = hdiag + dg + acc3
 __global__ void k_x_resid(DevProb P, DevState S, DevKKT K, const double *hx, const double *acc1,
                           const double *acc2, const double *acc3, double *part) {
-  __shared__ double sh[32 * 2];
+  __shared__ double sh[32 * 3];
   const double mu = K.mu;
-  double ss[2] = {0.0, 0.0};   // [all residual blocks of x, r_H only]
+  double ss[3] = {0.0, 0.0, 0.0};   // [bound residuals, r_H, bound complementarity]
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n; i += (int64_t)gridDim.x * blockDim.x) {
     const bool fl = P.haslx[i], fu = P.hasux[i];
     const double x = S.x[i];
@@ -458,11 +491,16 @@ __global__ void k_x_resid(DevProb P, DevState S, DevKKT K, const double *hx, con
     K.rH[i] = rH; K.rlx[i] = rlx; K.rux[i] = rux; K.rc3[i] = rc3; K.rc4[i] = rc4; K.dg[i] = dg;
     K.rhs[i] = r1 + acc2[i];
     K.diag[i] = P.hdiag[i] + dg + acc3[i];
-    ss[0] += rH * rH + rlx * rlx + rux * rux + rc3 * rc3 + rc4 * rc4;
+    ss[0] += rlx * rlx + rux * rux;
     ss[1] += rH * rH;
+    ss[2] += rc3 * rc3 + rc4 * rc4;
   }
-  block_sum<2>(ss, sh);
-  if (threadIdx.x == 0) { part[blockIdx.x] = ss[0]; part[NB + blockIdx.x] = ss[1]; }
+  block_sum<3>(ss, sh);
+  if (threadIdx.x == 0) {
+    part[blockIdx.x] = ss[0];
+    part[NB + blockIdx.x] = ss[1];
+    part[2 * NB + blockIdx.x] = ss[2];
+  }
 }
 
 // ---------------------------------------------------------------- step recovery and ratio test
@@ -629,12 +667,12 @@ kq_status hx_apply(kq_problem *h, const double *v, double *hx) {
     if (P.hdtype == KQ_F64) {
       k_zt<double><<<nbz, 256, 0, h->stream>>>(P, v, h->g);
       ++h->launches;
-      k_zg<double><<<NB, NT, 0, h->stream>>>(P, h->g, hx);
+      k_zg<double><<<NB, NT, 0, h->stream>>>(P, h->g, v, hx);
       ++h->launches;
     } else {
       k_zt<float><<<nbz, 256, 0, h->stream>>>(P, v, h->g);
       ++h->launches;
-      k_zg<float><<<NB, NT, 0, h->stream>>>(P, h->g, hx);
+      k_zg<float><<<NB, NT, 0, h->stream>>>(P, h->g, v, hx);
       ++h->launches;
     }
   } else {
@@ -709,8 +747,8 @@ kq_status assemble_enqueue(kq_problem *h) {
   KQ_CUDA(h, cudaMemsetAsync(h->acc1, 0, P.n * sizeof(double), h->stream));
   KQ_CUDA(h, cudaMemsetAsync(h->acc2, 0, P.n * sizeof(double), h->stream));
   KQ_CUDA(h, cudaMemsetAsync(h->acc3, 0, P.n * sizeof(double), h->stream));
-  KQ_CUDA(h, cudaMemsetAsync(h->red, 0, 4 * NB * sizeof(double), h->stream));
-  k_rows_resid<<<NB, NT, 0, h->stream>>>(P, h->S, h->K, h->t, h->tC, cf, h->red + 2 * NB);
+  KQ_CUDA(h, cudaMemsetAsync(h->red, 0, 5 * NB * sizeof(double), h->stream));
+  k_rows_resid<<<NB, NT, 0, h->stream>>>(P, h->S, h->K, h->t, h->tC, cf, h->red + 3 * NB);
   ++h->launches;
   if (P.hkind == KQ_H_CSR_LSQ) {
     // the rows of P (H x and, for ROWS_OF_P, the dose-limit rows)
@@ -732,13 +770,18 @@ kq_status assemble_enqueue(kq_problem *h) {
   k_x_resid<<<NB, NT, 0, h->stream>>>(P, h->S, h->K, h->hx, h->acc1, h->acc2, h->acc3, h->red);
   ++h->launches;
   KQ_CUDA(h, cudaGetLastError());
-  return reduce_async(h, 3, 0, 0);
+  return reduce_async(h, 5, 0, 10);
 }
 
-// after a stream synchronisation: |r|^2 (all blocks of Eq. (7)) and |r_H|^2
+// after a stream synchronisation: |r|^2 (all blocks of Eq. (7)) and |r_H|^2;
+// the section 5.2 infeasibilities (squared) go to h->inf2 = [primal, dual, compl]
 void assemble_finish(kq_problem *h, double *norm2, double *rH2) {
-  *norm2 = h->h_red[0] + h->h_red[2];
-  if (rH2) *rH2 = h->h_red[1];
+  const double *r = h->h_red + 10;   // [bound res, r_H, bound compl, row res, row compl]
+  *norm2 = r[0] + r[1] + r[2] + r[3] + r[4];
+  if (rH2) *rH2 = r[1];
+  h->inf2[0] = r[0] + r[3];
+  h->inf2[1] = r[1];
+  h->inf2[2] = r[2] + r[4];
   h->kkt_valid = true;
 }
 
@@ -847,6 +890,7 @@ void kq_default_ipm_opts(kq_ipm_opts *o) {
   o->timeout_s = 2.0;
   o->grid_ctas = 0;
   o->verbose = 0;
+  o->record = 0;
 }
 
 void kq_default_pcg_opts(kq_pcg_opts *o) {
@@ -952,8 +996,16 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
     P.k = H->cols;
     P.Z = up(H->val, (size_t)n * P.k * dtype_size(H->dtype));
     if (!P.Z) return fail(KQ_ERR_OOM, "Z");
-    if (H->dtype == KQ_F64) k_rownorm2<double><<<NB, NT, 0, s>>>(n, P.k, (const double *)P.Z, hdiag);
-    else k_rownorm2<float><<<NB, NT, 0, s>>>(n, P.k, (const float *)P.Z, hdiag);
+    if (H->w) {
+      P.zw = (const double *)up(H->w, P.k * sizeof(double));
+      if (!P.zw) return fail(KQ_ERR_OOM, "Z weights");
+    }
+    if (H->d0) {
+      P.d0 = (const double *)up(H->d0, n * sizeof(double));
+      if (!P.d0) return fail(KQ_ERR_OOM, "H0");
+    }
+    if (H->dtype == KQ_F64) k_rownorm2<double><<<NB, NT, 0, s>>>(n, P.k, (const double *)P.Z, P.zw, P.d0, hdiag);
+    else k_rownorm2<float><<<NB, NT, 0, s>>>(n, P.k, (const float *)P.Z, P.zw, P.d0, hdiag);
   } else {
     P.nP = H->rows;
     int64_t nnz = H->nnz;
@@ -1010,6 +1062,8 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
     return fail(KQ_ERR_NUMERIC, "H or p has NaN/Inf");
   const double sigma = 1.0 / std::max(1.0, std::max(hmax, pmax));
   h->sigma = sigma;
+  h->sigma_create = sigma;
+  h->hmax = hmax;
   k_scale_vec<<<NB, NT, 0, s>>>(n, pd, nullptr, sigma);
   k_scale_vec<<<NB, NT, 0, s>>>(n, hdiag, nullptr, sigma);
   P.p = pd;
@@ -1114,6 +1168,70 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
   h->mu = 1.0;
   h->mu_exp = 0;
   *out = h;
+  return KQ_OK;
+}
+
+kq_status qp_update(kq_handle h, const double *p, const double *lA, const double *uA,
+                    const double *b) {
+  if (!h) return kq_fail(nullptr, KQ_ERR_ARG, "null handle");
+  DevProb &P = h->P;
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n, m = h->m, me = h->me;
+  if (p) {
+    double *pd = const_cast<double *>(P.p);
+    KQ_CUDA(h, cudaMemcpyAsync(pd, p, n * sizeof(double), cudaMemcpyDefault, s));
+    k_max_abs<<<NB, NT, 0, s>>>(n, pd, h->red);
+    k_scale_vec<<<NB, NT, 0, s>>>(NB, h->red, nullptr, -1.0);
+    double pm[1];
+    if (fetch(h, 1, {1}, pm) != KQ_OK) return kq_fail(h, KQ_ERR_CUDA, "qp_update: reduction");
+    const double pmax = -pm[0];
+    if (!(pmax == pmax) || isinf(pmax)) return kq_fail(h, KQ_ERR_NUMERIC, "qp_update: p has NaN/Inf");
+    // the same objective scale rule as qp_create
+    const double sigma = 1.0 / std::max(1.0, std::max(h->hmax, pmax));
+    const double ratio = sigma / h->sigma;
+    k_scale_vec<<<NB, NT, 0, s>>>(n, pd, nullptr, sigma);
+    if (ratio != 1.0) {
+      if (P.hkind == KQ_H_CSR_LSQ) {
+        k_scale_vec<<<NB, NT, 0, s>>>(P.nP, const_cast<double *>(P.w2), nullptr, ratio);
+        P.wfac = sigma / h->sigma_create;
+        P.wfac32 = (float)P.wfac;
+      } else {
+        k_scale_vec<<<NB, NT, 0, s>>>(n, const_cast<double *>(P.hdiag), nullptr, ratio);
+        P.hscale = sigma;
+      }
+      h->sigma = sigma;
+    }
+  }
+  if (m > 0 && (lA || uA)) {
+    double *lAd = const_cast<double *>(P.lA), *uAd = const_cast<double *>(P.uA);
+    if (lA) KQ_CUDA(h, cudaMemcpyAsync(lAd, lA, m * sizeof(double), cudaMemcpyDefault, s));
+    if (uA) KQ_CUDA(h, cudaMemcpyAsync(uAd, uA, m * sizeof(double), cudaMemcpyDefault, s));
+    // the row scaling of qp_create applied to the replaced bounds (the others
+    // are stored scaled already), then the flags from finiteness
+    k_flags_scaled<<<NB, NT, 0, s>>>(m, lAd, uAd, lA != nullptr, uA != nullptr, P.rhoA,
+                                      const_cast<uint8_t *>(P.hasl), const_cast<uint8_t *>(P.hasu));
+  }
+  if (me > 0 && b) {
+    double *bd = const_cast<double *>(P.b);
+    KQ_CUDA(h, cudaMemcpyAsync(bd, b, me * sizeof(double), cudaMemcpyDefault, s));
+    k_scale_vec<<<NB, NT, 0, s>>>(me, bd, h->rhoC, 0.0);
+  }
+  KQ_CUDA(h, cudaGetLastError());
+  KQ_CUDA(h, cudaStreamSynchronize(s));
+  h->solved = false;
+  h->state_set = false;
+  h->kkt_valid = false;
+  return KQ_OK;
+}
+
+kq_status qp_iteration_log(kq_handle h, kq_ipm_iter *out, int cap, int *count) {
+  if (!h) return kq_fail(nullptr, KQ_ERR_ARG, "null handle");
+  if (!h->record && h->iter_log.empty())
+    return kq_fail(h, KQ_ERR_STATE, "no ipm_solve with opts.record = 1 ran");
+  const int k = (int)h->iter_log.size();
+  if (count) *count = k;
+  if (out)
+    for (int i = 0; i < std::min(k, std::max(cap, 0)); ++i) out[i] = h->iter_log[i];
   return KQ_OK;
 }
 
@@ -1264,13 +1382,51 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
   kq_status final = KQ_ERR_IPM_MAXIT;
   const DevProb &P = h->P;
   int it = 0;
+  // Mixed precision pays where a product is bandwidth-bound.  Once a Newton
+  // solve needed FP64 correction iterations (its FP32 passes stalled) and an
+  // FP64 product costs less than twice an FP32 iteration (a latency-bound
+  // problem), the rest of the solve runs in FP64 (KQ_MIXED_SWITCH=0: never).
+  bool to_f64 = false;
+  const char *msw = getenv("KQ_MIXED_SWITCH");
+  const bool allow_switch = !(msw && atoi(msw) == 0);
+  h->record = o.record != 0;
+  h->iter_log.clear();
   for (it = 1; it <= o.ipm_maxit; ++it) {
     kq_pcg_stats ps{};
+    kq_ipm_iter rec{};
+    if (h->record) {
+      // max diag(K) / min diag(K) of this Newton system
+      k_minmax<<<NB, NT, 0, h->stream>>>(h->nkp, h->K.diag, h->red);
+      ++h->launches;
+      double mm[2];
+      if (fetch(h, 2, {1, 1}, mm) == KQ_OK && mm[0] > 0.0) rec.diag_ratio = -mm[1] / mm[0];
+      rec.it = it;
+      rec.mu = mu;
+    }
+    po.precision = to_f64 ? KQ_PREC_F64 : o.precision;
     rc = pcg_solve(h, h->K.rhs, h->z, po, &ps);
+    if (h->record) {
+      rec.pcg_iters = ps.iters;
+      rec.pcg_iters_f64 = ps.iters_f64;
+      rec.pcg_rel_res = ps.rel_res;
+      rec.pcg_ms = ps.kernel_ms;
+      rec.lanczos_steps = h->lz_steps;
+      rec.lanczos_min = h->lz_min;
+      rec.lanczos_max = h->lz_max;
+      rec.kappa_jacobi = h->lz_min > 0.0 ? h->lz_max / h->lz_min : 0.0;
+    }
+    if (o.precision == KQ_PREC_MIXED && !to_f64 && allow_switch && ps.iters_f64 > 0) {
+      const double t32 = (ps.kernel_ms - ps.kernel_ms_f64) / std::max(1, ps.iters - ps.iters_f64);
+      const double t64 = ps.kernel_ms_f64 / std::max(1, ps.products_f64);
+      if (t64 < 2.0 * t32) {
+        to_f64 = true;
+        st.switched_to_f64 = it;
+      }
+    }
     st.pcg_iters += ps.iters;
     st.pcg_kernel_ms += ps.kernel_ms;
     st.pcg_launches += 2 * ps.passes;
-    st.pcg_products += ps.iters + ps.passes;
+    st.pcg_products += ps.products;
     st.pcg_iters_f64 += ps.iters_f64;
     st.pcg_products_f64 += ps.products_f64;
     st.pcg_kernel_ms_f64 += ps.kernel_ms_f64;
@@ -1288,6 +1444,15 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
     const double rn = sqrt(n2);
     if (!(rn == rn)) { final = kq_fail(h, KQ_ERR_NUMERIC, "residual norm is NaN"); break; }
     st.res_norm = rn;
+    if (h->record) {
+      rec.res_norm = rn;
+      rec.primal_inf = sqrt(h->inf2[0]);
+      rec.dual_inf = sqrt(h->inf2[1]);
+      rec.compl_inf = sqrt(h->inf2[2]);
+      rec.alpha_x = ax;
+      rec.alpha_lam = al;
+      h->iter_log.push_back(rec);
+    }
     if (o.verbose)
       fprintf(stderr, "ipm %3d mu %.0e |r| %.3e ax %.4f al %.4f pcg %5d passes %d rel %.2e %.2f ms\n",
               it, mu, rn, ax, al, ps.iters, ps.passes, ps.rel_res, ps.kernel_ms);
@@ -1307,7 +1472,9 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
   {
     double rH2 = 0.0;
     assemble_norms(h, &n2, &rH2);
+    st.primal_inf = sqrt(h->inf2[0]);
     st.dual_inf = sqrt(rH2);
+    st.compl_inf = sqrt(h->inf2[2]);
     st.res_norm = sqrt(n2);
   }
   // outputs

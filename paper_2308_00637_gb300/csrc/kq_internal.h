@@ -11,6 +11,9 @@ struct DevProb {
   int64_t n = 0, m = 0, me = 0, nkp = 0;
   int hkind = 0, hdtype = 0;
   double hscale = 1.0;               // sigma (DENSE, LOWRANK): H_scaled = hscale * H
+  double wfac = 1.0;                 // CSR_LSQ: sigma / (sigma at create), applied to the
+                                     // FP32 row tables (the FP64 w2 is rescaled in place)
+  float wfac32 = 1.f;                // wfac in FP32 (FP32 products)
   // DENSE H (scaled by sigma), n x n row-major with leading dimension hld
   // (rows padded with zeros to a multiple of 8 entries; 0 means n)
   const void *Hd = nullptr;
@@ -23,9 +26,11 @@ struct DevProb {
   const double *w2 = nullptr;
   const int32_t *prow2a = nullptr;   // nP: A-row id or -1
   const int32_t *arows = nullptr;    // m: P row of A row
-  // LOWRANK: H = Zs Zs', Zs = sqrt(sigma) Z, n x k row-major
+  // LOWRANK: H = sigma (Z diag(zw) Z' + diag(d0)), Z n x k row-major
   int64_t k = 0;
   const void *Z = nullptr;
+  const double *zw = nullptr;        // k column weights (null: all 1)
+  const double *d0 = nullptr;        // n diagonal H0, unscaled (null: 0)
   // general rows, stored unscaled (the row scale rhoA is applied on the fly):
   // DENSE m x n row-major (leading dimension ald), or CSR (arowptr, acol, aval)
   int akind = 0, adtype = 0;
@@ -117,6 +122,8 @@ __host__ __device__ inline CsrLayout csr_layout(int win_cap, int a_cap, int ch_c
   return L;
 }
 
+constexpr int KQ_LANCZOS_CAP = 5000;   // PCG iterations whose coefficients are kept
+
 // Work space of the persistent PCG kernels.
 struct PcgWork {
   int G = 0;                   // CTAs of the cooperative launch
@@ -130,6 +137,7 @@ struct PcgWork {
   double *g64 = nullptr;       // k + me (LOWRANK)
   double *coefA = nullptr;     // m (DENSE column pass)
   double *dinv = nullptr;      // nkp: 1 / diag(K) of the current solve
+  double *lanczos = nullptr;   // 2 * KQ_LANCZOS_CAP: PCG alpha, beta (records)
   float *p32_0 = nullptr, *p32_1 = nullptr, *y32 = nullptr;  // nkp FP32 copies (register-streamed CSR)
   double *slots = nullptr;     // 4 * G
   unsigned int *bar = nullptr; // [count, gen]
@@ -166,6 +174,8 @@ struct kq_problem {
   std::string err;
   int64_t n = 0, m = 0, me = 0, nkp = 0;
   double sigma = 1.0;
+  double sigma_create = 1.0;    // sigma when the row tables were built
+  double hmax = 0.0;            // max_i H_ii of the unscaled H (for sigma)
   DevProb P;
   DevState S;
   DevKKT K;
@@ -180,6 +190,7 @@ struct kq_problem {
   double *red = nullptr;        // reduction partials
   double *red_out = nullptr;    // reduction results (device)
   double *h_red = nullptr;      // pinned host mirror of results
+  double inf2[3] = {0, 0, 0};   // squared primal, dual, complementarity norms (section 5.2)
   double *rhoC = nullptr;       // equality row scales (me)
   int *dflags = nullptr;        // reduction kind flags (8)
   bool state_set = false;       // qp_set_state supplied the starting iterate
@@ -193,6 +204,12 @@ struct kq_problem {
   float last_kernel_ms = 0.f;   // device time of this handle's last persistent PCG launch
   long long pcg_launches = 0;   // persistent PCG launches (solve + apply)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  // per-IPM-iteration records (opts.record)
+  bool record = false;          // the current ipm_solve keeps records
+  bool lz_on = false;           // the next PCG launch writes its alpha, beta
+  int lz_steps = 0;             // Lanczos estimates of the last recorded pass
+  double lz_min = 0.0, lz_max = 0.0;
+  std::vector<kq_ipm_iter> iter_log;
 };
 
 // ---------------------------------------------------------------- host helpers
@@ -212,6 +229,8 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
 // out = K v in FP64 (prec = KQ_PREC_F64) or mixed arithmetic.
 kq_status pcg_apply(kq_problem *h, const double *v, double *out, int prec, float *ms);
 double pcg_last_kernel_ms(const kq_problem *h);
+// Lanczos extreme eigenvalues from the alpha, beta of the last recorded pass
+void lanczos_extremes(kq_problem *h, int iters);
 // Work buffers of one persistent PCG launch, provided by the caller.
 struct PcgRawWork {
   double *r, *y, *pb0, *pb1, *qlam, *slots, *resn;

@@ -27,7 +27,7 @@ constexpr int64_t KQ_STATIC_DOUBLES = 5 * KQ_STATIC_MAX_NKP + 2 * KQ_STATIC_MAX_
                                       4 * KQ_STATIC_MAX_CTAS + 2 + 16;
 
 // The scratch array: every GPU that loads the library holds it until exit
-// (about 0.78 MB).  All calls share it.
+// (about 0.76 MB).  All calls share it.
 static __device__ __align__(256) double g_kq_static_scratch[KQ_STATIC_DOUBLES];
 
 // Device address of the array, looked up once per device (host code must not

@@ -23,6 +23,7 @@
 #include "common.cuh"
 #include "kq_internal.h"
 #include <algorithm>
+#include <cmath>
 #include <cstdlib>
 #include <vector>
 
@@ -67,6 +68,8 @@ struct PcgArgs {
   int pf_dist;                  // L2 prefetch distance in warp steps (0: off, the default)
   double *dinv;                 // 1 / diag(K), formed at the start of a solve (or null)
   float *p32_0, *p32_1, *y32;   // FP32 copies of p (paired with pb0 / pb1) and y (or null)
+  double *lanczos;              // (alpha_j, beta_j) per iteration, or null (not recorded)
+  int lanczos_cap;              // iterations that fit in lanczos
 };
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
@@ -425,7 +428,9 @@ struct OpLowrank {
     // phase A2: (Z g)_i + sum_e C_ei (2 t_e / mu + p_e)
     double *cf = ps + a.win_cap;                          // me coefficients
     T *gs = reinterpret_cast<T *>(cf + me + 1);           // g = [Z C']'p_x
-    for (int64_t c = tid; c < kk; c += blockDim.x) gs[c] = (T)(__ldcg(a.g + c) * (c < k ? P.hscale : 1.0));
+    // g = [Z C']'p_x, the Z part weighted by sigma zw
+    for (int64_t c = tid; c < kk; c += blockDim.x)
+      gs[c] = (T)(__ldcg(a.g + c) * (c < k ? P.hscale * (P.zw ? P.zw[c] : 1.0) : 1.0));
     for (int64_t e = tid; e < me; e += blockDim.x) {
       const double t = __ldcg(a.g + k + e);
       const double pe = ldcg(ysrc + n + e) + beta * ldcg(pold + n + e);
@@ -443,6 +448,7 @@ struct OpLowrank {
       s = warp_sum(s);
       if (lane == 0) {
         double hz = (double)s;
+        if (P.d0) hz += P.hscale * P.d0[i] * ps[i - r0];   // diagonal H0
         for (int64_t e = 0; e < me; ++e) hz += P.Cd[e * n + i] * cf[e];
         if (P.akind == KQ_A_CSR) atomicAdd(accg + i, (T)hz);   // shared with the A-row scatter
         else accg[i] = (T)hz;
@@ -647,8 +653,9 @@ struct OpCsrStaged {
                                                const T *apl, const T *apu, const uint8_t *afl,
                                                int lane, T &pqt) {
     T u;
-    if constexpr (sizeof(T) == 4) u = d.w2hi * dot;
-    else u = ((double)d.w2hi + (double)d.w2lo) * dot;
+    // the row tables hold 2 sigma w of qp_create; wfac = sigma_now / sigma_create
+    if constexpr (sizeof(T) == 4) u = (d.w2hi * a.P.wfac32) * dot;
+    else u = (((double)d.w2hi + (double)d.w2lo) * a.P.wfac) * dot;
     if (d.a >= 0) {
       const DevProb &P = a.P;
       const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
@@ -776,7 +783,7 @@ struct OpCsrStaged {
       block_sum<1>(part, shl);
       if (tid == 0) {
         const double dd = part[0];
-        double ud = ((double)d.w2hi + (double)d.w2lo) * dd;
+        double ud = ((double)d.w2hi + (double)d.w2lo) * P.wfac * dd;
         if (d.a >= 0) {
           const int ai = d.a;
           const double rho = P.rhoA[ai];
@@ -1375,12 +1382,31 @@ __device__ __forceinline__ double slot_sum_w0(const double *s, int G) {
   return warp_sum(v);
 }
 
-// Sum of two slot arrays by warp 0 (fixed order); result in warp 0.
+// Sum of two slot arrays by warp 0 (the fixed order of slot_sum_w0); both
+// arrays' loads are issued before any arithmetic, so the two sums cost one
+// memory round trip after the grid barrier instead of two.  Result in warp 0.
 __device__ __forceinline__ void slots2_t0(const double *s0, const double *s1, int G, double &o0,
                                           double &o1) {
   if (threadIdx.x < 32) {
-    o0 = slot_sum_w0(s0, G);
-    o1 = slot_sum_w0(s1, G);
+    double v0 = 0.0, v1 = 0.0;
+    for (int b = 0; b < G; b += 160) {
+      double t[5], u[5];
+#pragma unroll
+      for (int k = 0; k < 5; ++k) {
+        const int i = b + threadIdx.x + 32 * k;
+        t[k] = (i < G) ? __ldcg(s0 + i) : 0.0;
+        u[k] = (i < G) ? __ldcg(s1 + i) : 0.0;
+      }
+      v0 += ((t[0] + t[1]) + (t[2] + t[3])) + t[4];
+      v1 += ((u[0] + u[1]) + (u[2] + u[3])) + u[4];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      v0 += __shfl_xor_sync(0xffffffffu, v0, o);
+      v1 += __shfl_xor_sync(0xffffffffu, v1, o);
+    }
+    o0 = v0;
+    o1 = v1;
   }
 }
 
@@ -1489,6 +1515,7 @@ __device__ void pcg_body(const PcgArgs &a, const int cta, const int G, unsigned 
         if (bad && cta == 0) atomicCAS(a.bar.err, 0, bad);
         sh[0] = bad ? 0.0 : rho / pqt;
         sh[1] = (double)bad;
+        if (a.lanczos && cta == 0 && it < a.lanczos_cap) a.lanczos[2 * it] = sh[0];
       }
       __syncthreads();
       const double alpha = sh[0];
@@ -1543,6 +1570,7 @@ __device__ void pcg_body(const PcgArgs &a, const int cta, const int G, unsigned 
       if (tid == 0) {
         rr = rrn;
         const double bt = rho_new / rho;
+        if (a.lanczos && cta == 0 && it < a.lanczos_cap) a.lanczos[2 * it + 1] = bt;
         rho = rho_new;
         bool st = rr <= a.tol2 * bb || it + 1 >= a.maxit;
         // FP32 correction passes: hand over to the FP64 pass once they stagnate
@@ -1730,6 +1758,10 @@ kq_status launch(kq_problem *h, int prec, const double *rhs, double *z, double t
   int threads = W.threads;
   a.dinv = W.dinv;
   a.rw2lo = W.rw2lo;
+  if (h->lz_on && !apply) {
+    a.lanczos = W.lanczos;
+    a.lanczos_cap = KQ_LANCZOS_CAP;
+  }
   if (prec == KQ_PREC_MIXED && W.rows_ok) {
     f = pcg_kernel<OpCsrRows, float>;
     smem = W.smem_rows;
@@ -1919,12 +1951,17 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
     const kq_problem *hj = hs[idx[j]];
     t = (int)std::min<int64_t>(t, ceil_div64(hj->n + hj->m + hj->me, 32));
     t = std::min(t, hj->num_sms);     // the problem's slot buffer holds up to num_sms CTAs
-    if (t < 2 || used + t > G - 1) break;
+    // keep one CTA for the problems packed onto single CTAs, unless none is
+    // left to pack; a team that does not fit is shrunk, not dropped (a
+    // dropped problem would run on one CTA)
+    const int room = (q + 1 < order.size()) ? G - 1 - used : G - used;
+    t = std::min(t, room);
+    if (t < 2) break;
     teams.push_back(TeamInfo{used, t, 0, 0});
     members.push_back({j});
     used += t;
   }
-  const int nsingle = std::max(1, G - used);
+  const int nsingle = (q < order.size()) ? std::max(1, G - used) : 0;
   const int first_single = (int)teams.size();
   std::vector<double> load(nsingle, 0.0);
   for (int c = 0; c < nsingle; ++c) {
@@ -2476,6 +2513,7 @@ kq_status pcg_setup(kq_problem *h, int grid_ctas) {
   W.g64 = dalloc<double>(h, P.k + P.me + 1);
   W.coefA = dalloc<double>(h, P.m + 1);
   W.dinv = dalloc<double>(h, nkp);
+  W.lanczos = dalloc<double>(h, 2 * (size_t)KQ_LANCZOS_CAP);
   if (W.rows_ok) {
     W.p32_0 = dalloc<float>(h, nkp);
     W.p32_1 = dalloc<float>(h, nkp);
@@ -2502,6 +2540,58 @@ kq_status pcg_apply(kq_problem *h, const double *v, double *out, int prec, float
   kq_status st = launch(h, prec, v, out, 0.0, 0, 1, nullptr, nullptr, nullptr);
   if (ms) *ms = h->last_kernel_ms;
   return st;
+}
+
+// Extreme eigenvalues of the Lanczos tridiagonal matrix of a PCG pass (the
+// PCG-Lanczos relation: T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1},
+// T_{j,j+1} = sqrt(beta_j)/alpha_j), by Sturm-sequence bisection.  Results in
+// h->lz_min, h->lz_max, h->lz_steps (0 when the pass ran no iteration).
+namespace {
+int sturm_count(const std::vector<double> &d, const std::vector<double> &e2, double x) {
+  int c = 0;
+  double q = 1.0;
+  for (size_t i = 0; i < d.size(); ++i) {
+    q = d[i] - x - (i > 0 ? e2[i - 1] / q : 0.0);
+    if (q == 0.0) q = -1e-300;
+    if (q < 0.0) ++c;
+  }
+  return c;
+}
+}  // namespace
+
+void lanczos_extremes(kq_problem *h, int iters) {
+  h->lz_steps = 0;
+  h->lz_min = h->lz_max = 0.0;
+  const int k = std::min(iters, (int)KQ_LANCZOS_CAP);
+  if (k <= 0) return;
+  std::vector<double> ab(2 * (size_t)k);
+  if (cudaMemcpy(ab.data(), h->W.lanczos, ab.size() * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return;
+  std::vector<double> d(k), e2(std::max(k - 1, 1), 0.0);
+  for (int j = 0; j < k; ++j) {
+    const double aj = ab[2 * j], bprev = j > 0 ? ab[2 * (j - 1) + 1] : 0.0;
+    if (!(aj > 0.0)) return;
+    d[j] = 1.0 / aj + (j > 0 ? bprev / ab[2 * (j - 1)] : 0.0);
+    if (j + 1 < k) e2[j] = ab[2 * j + 1] / (aj * aj);   // (sqrt(beta_j) / alpha_j)^2
+  }
+  // Gershgorin interval
+  double lo = 1e300, hi = -1e300;
+  for (int j = 0; j < k; ++j) {
+    const double r = (j > 0 ? sqrt(e2[j - 1]) : 0.0) + (j + 1 < k ? sqrt(e2[j]) : 0.0);
+    lo = std::min(lo, d[j] - r);
+    hi = std::max(hi, d[j] + r);
+  }
+  auto kth = [&](int target) {   // smallest x with count(x) >= target
+    double a = lo, b = hi;
+    for (int t = 0; t < 200 && b - a > 1e-15 * std::max(fabs(a), fabs(b)); ++t) {
+      const double m = 0.5 * (a + b);
+      if (sturm_count(d, e2, m) >= target) b = m; else a = m;
+    }
+    return 0.5 * (a + b);
+  };
+  h->lz_min = kth(1);
+  h->lz_max = kth(k);
+  h->lz_steps = k;
 }
 
 // Jacobi PCG with optional FP32-matvec correction solves and FP64 residual
@@ -2536,12 +2626,20 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
     const int budget = o.maxit - total;
     if (budget <= 0) break;
     int it = 0;
+    h->lz_on = h->record && pass == 0;
     rc = launch(h, prec, res, dz, rel, budget, 0, &it, nullptr, nullptr);
+    if (h->lz_on) {
+      h->lz_on = false;
+      lanczos_extremes(h, it);
+    }
     s.kernel_ms += h->last_kernel_ms;
     total += it;
+    // products inside the launch: one per iteration
+    const int prods = it;
+    s.products += prods + 1;   // and the FP64 residual product below
     if (prec == KQ_PREC_F64) {
       s.iters_f64 += it;
-      s.products_f64 += it;
+      s.products_f64 += prods;
       s.kernel_ms_f64 += h->last_kernel_ms;
       s.launches_f64 += 1;
     }

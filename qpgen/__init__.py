@@ -13,7 +13,10 @@ structures:
 * ``dense``   : H is an explicit symmetric n x n matrix;
 * ``csr_lsq`` : H = 2 P^T W P with P a CSR matrix (rows x n) and W = diag(w),
                 the least-squares dose objective sum_i w_i (P x - d)_i^2;
-* ``lowrank`` : H = Z Z^T with Z a dense n x k matrix (linear-kernel SVM dual).
+* ``lowrank`` : H = Z W Z^T + H0 with Z a dense n x k matrix, W = diag(zw)
+                (default I) and H0 = diag(d0) (default 0): the linear-kernel SVM
+                dual (Z Z^T), or a quasi-Newton (BFGS) Hessian of the form
+                H0 + U W U^T.
 
 A constraint matrix A is either dense, a CSR matrix, or a subset of the rows of
 P (``a_rows``), which is how dose-limit constraints reuse the dose matrix.
@@ -44,6 +47,8 @@ class QPData:
     P: Optional[sp.csr_matrix] = None   # csr_lsq: float32 CSR, rows x n
     w: Optional[np.ndarray] = None      # csr_lsq: float64 row weights
     Z: Optional[np.ndarray] = None      # lowrank: float32 n x k
+    zw: Optional[np.ndarray] = None     # lowrank: column weights W (None = 1)
+    d0: Optional[np.ndarray] = None     # lowrank: diagonal H0 (None = 0)
     akind: str = "none"             # 'none' | 'dense' | 'csr' | 'rows_of_p'
     A: object = None                # dense ndarray (float64) or csr (float32)
     a_rows: Optional[np.ndarray] = None  # rows_of_p: int32 row ids into P
@@ -88,7 +93,9 @@ class QPData:
             P = self.P.astype(np.float64)
             return np.asarray((2.0 * (P.T @ sp.diags(self.w) @ P)).todense())
         Z = self.Z.astype(np.float64)
-        return Z @ Z.T
+        zw = np.ones(Z.shape[1]) if self.zw is None else np.asarray(self.zw, float)
+        d0 = np.zeros(self.n) if self.d0 is None else np.asarray(self.d0, float)
+        return (Z * zw) @ Z.T + np.diag(d0)
 
     def objective(self, x: np.ndarray) -> float:
         """1/2 x^T H x + p^T x, evaluated from the operator's structure."""
@@ -99,7 +106,9 @@ class QPData:
             Hx = 2.0 * (P.T @ (self.w * (P @ x)))
         else:
             Z = self.Z.astype(np.float64)
-            Hx = Z @ (Z.T @ x)
+            zw = np.ones(Z.shape[1]) if self.zw is None else np.asarray(self.zw, float)
+            d0 = np.zeros(self.n) if self.d0 is None else np.asarray(self.d0, float)
+            Hx = Z @ (zw * (Z.T @ x)) + d0 * x
         return float(0.5 * x @ Hx + self.p @ x)
 
 
@@ -387,7 +396,8 @@ def with_general_rows(qp: QPData, m: int, nnz_row: int, me: int, x_ref: np.ndarr
     b = C @ x_ref if me else None
     meta = dict(qp.meta)
     meta.update({"general_rows_seed": seed, "x_ref": x_ref})
-    return QPData(n=n, hkind=qp.hkind, p=qp.p, H=qp.H, P=qp.P, w=qp.w, Z=qp.Z, akind="csr",
+    return QPData(n=n, hkind=qp.hkind, p=qp.p, H=qp.H, P=qp.P, w=qp.w, Z=qp.Z, zw=qp.zw,
+                  d0=qp.d0, akind="csr",
                   A=A, lA=lA, uA=uA, C=C, b=b, lx=qp.lx, ux=qp.ux, meta=meta)
 
 
@@ -423,3 +433,26 @@ def svm_qp_general(N: int = 400, dim: int = 12, m: int = 30, nnz_row: int = 25,
     q = with_general_rows(base, m, nnz_row, 0, x_ref, seed + 1)
     q.C, q.b = base.C, base.b
     return q
+
+
+# ---------------------------------------------------------------------------
+# Quasi-Newton Hessian (section 2.1: the RT objectives are nonlinear and the
+# QP subproblem's Hessian is a BFGS approximation H0 + U W U^T).  H0 =
+# diag(d0), d0 ~ U(0.5, 2); U n x k with entries N(0,1)/sqrt(k) in float32;
+# W = diag(w), w ~ U(0.1, 1); p ~ N(0,1); bounds 0 <= x <= 1 and, with
+# `rows` > 0, sparse positive (dose-like) general rows with two-sided limits
+# around x_ref = 1/2.  Draw order: d0, U, w, p, then the rows.
+# ---------------------------------------------------------------------------
+def bfgs_qp(n: int = 3000, k: int = 20, rows: int = 200, nnz_row: int = 40,
+            seed: int = 41) -> QPData:
+    rng = np.random.default_rng(seed)
+    d0 = rng.uniform(0.5, 2.0, n)
+    U = (rng.standard_normal((n, k)) / np.sqrt(k)).astype(np.float32)
+    w = rng.uniform(0.1, 1.0, k)
+    p = rng.standard_normal(n)
+    qp = QPData(n=n, hkind="lowrank", p=p, Z=U, zw=w, d0=d0, akind="none",
+                lx=_full(n, 0.0), ux=_full(n, 1.0), meta={"seed": seed})
+    if rows:
+        qp = with_general_rows(qp, rows, nnz_row, 0, np.full(n, 0.5), seed + 1, two_sided=1.0,
+                               positive=True, dtype=np.float32)
+    return qp

@@ -135,3 +135,56 @@ def test_config4_adjoint_fd_and_oracle(kq):
     # the FD of the solver output carries an O(mu) non-smoothness near degenerate
     # constraints (measured median 0.7% at h=1e-4); a wrong sign or scale is O(1)
     assert best <= 2e-2, errs
+
+
+@pytest.mark.parametrize("name,pfac", [("dense_eq", 3.0), ("csr", 50.0)])
+def test_qp_update_matches_fresh_create(kq, name, pfac):
+    """qp_update replaces p, lA, uA (and b) in place; the solve equals the
+    oracle's solve of the changed problem.  pfac is large enough that |p|_inf
+    sets a new objective scale sigma (the CSR operator's FP32 row tables keep
+    their create-time weights and take the ratio on the fly)."""
+    import copy
+    import oracle
+    qp = SMALL[name]()
+    h = kq.create_from(qp)
+    sig0, _, _ = kq.qp_scaling(h)
+    q2 = copy.copy(qp)
+    q2.p = pfac * qp.p
+    if qp.m:
+        q2.lA = qp.lA - 0.05 * np.abs(qp.lA) - 0.01
+    kq.qp_update(h, q2.p, q2.lA if qp.m else None, None, None)
+    sig1, _, _ = kq.qp_scaling(h)
+    assert sig1 != sig0 and sig1 == pytest.approx(oracle.scale(q2).sigma, rel=1e-14)
+    for prec in (0, 1):
+        x = np.zeros(qp.n)
+        rc, st = kq.ipm_solve(h, kq.default_ipm_opts(precision=prec), x=x)
+        res = oracle.ipm_solve(q2)
+        f, fr = q2.objective(x), q2.objective(res.x)
+        assert rc == kq.KQ_OK and st.mu_final == pytest.approx(res.mu)
+        assert abs(f - fr) <= 1e-6 * (1 + abs(fr)), (prec, f, fr)
+    kq.qp_destroy(h)
+
+
+def test_qp_layer_reuses_handles(kq):
+    """A training-style loop: forward/backward pairs with a changing p reuse
+    one device handle; each forward equals a fresh solve of that p."""
+    import torch
+    from paper_2308_00637_gb300 import _pool
+    qp = SMALL["dense_eq"]()
+    dev = "cuda"
+    lA = torch.tensor(qp.lA, device=dev)
+    uA = torch.tensor(qp.uA, device=dev)
+    b = torch.tensor(qp.b, device=dev)
+    rng = np.random.default_rng(8)
+    for step in range(3):
+        p0 = qp.p + 0.1 * step * rng.standard_normal(qp.n)
+        p = torch.tensor(p0, device=dev, requires_grad=True)
+        x = kq.qp_layer(qp, p, lA, uA, b)
+        x.sum().backward()
+        import copy
+        q2 = copy.copy(qp)
+        q2.p = p0
+        _, _, out = kq.solve(q2)
+        assert np.max(np.abs(x.detach().cpu().numpy() - out["x"])) <= 1e-8 * (1 + np.max(np.abs(out["x"])))
+        assert torch.isfinite(p.grad).all()
+    assert _pool(qp).created == 1

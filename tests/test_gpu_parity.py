@@ -35,6 +35,8 @@ PROBLEMS = {
     "dense_csrA_eq": lambda: qpgen.dense_qp_general(),
     "csr_csrA_eq": lambda: qpgen.dose_qp_general(),
     "lowrank_csrA_eq": lambda: qpgen.svm_qp_general(),
+    # quasi-Newton Hessian H0 + U W U' (section 2.1) with sparse dose-like rows
+    "lowrank_bfgs": lambda: qpgen.bfgs_qp(800, 10, 60, 15, seed=43),
 }
 
 

@@ -168,7 +168,8 @@ def test_K_symmetric_positive_definite(seed):
     lambda: qpgen.tiny_qp(6, 4, 11, me=1),
     lambda: qpgen.dose_qp(300, 40, 8, 10, 12, seed=12),
     lambda: qpgen.svm_qp(60, 5, seed=13),
-], ids=["dense", "csr_lsq", "lowrank"])
+    lambda: qpgen.bfgs_qp(50, 6, 8, 7, seed=14),
+], ids=["dense", "csr_lsq", "lowrank", "lowrank_weighted_diag"])
 def test_matrix_free_apply_and_diag(maker):
     qp = maker()
     S = I.scale(qp)
@@ -184,6 +185,7 @@ def test_matrix_free_apply_and_diag(maker):
 @pytest.mark.parametrize("maker,solver", [
     (lambda: qpgen.dose_qp(600, 80, 12, 15, 30, seed=21), "schur_banded"),
     (lambda: qpgen.svm_qp(120, 6, seed=22), "schur_woodbury"),
+    (lambda: qpgen.bfgs_qp(150, 7, 25, 9, seed=24), "schur_woodbury"),
     (lambda: qpgen.dense_qp(40, 20, seed=23), "schur_dense"),
 ])
 def test_structured_direct_solvers(maker, solver):
@@ -490,3 +492,29 @@ def test_duality_gap_is_primal_minus_dual_objective():
     assert met["gap"] == pytest.approx(f - g + x @ rH, rel=1e-10, abs=1e-12)
     # converged: the gap is of the order of the final barrier parameter
     assert 0.0 < met["gap"] < 1e-5
+
+
+def test_jacobi_scaled_eigenvalues_closed_form():
+    """[[4, 2], [2, 1 + 1e-2]] scaled by its diagonal is [[1, c], [c, 1]] with
+    c = 2 / sqrt(4 (1.01)): eigenvalues 1 -+ c (section 5.3's conditioning of
+    the Jacobi-preconditioned system)."""
+    K = np.array([[4.0, 2.0], [2.0, 1.01]])
+    c = 2.0 / np.sqrt(4.0 * 1.01)
+    ev = I.jacobi_scaled_eigenvalues(K)
+    assert np.allclose(ev, [1 - c, 1 + c], rtol=1e-13, atol=0)
+    # a diagonal K is perfectly conditioned after Jacobi scaling
+    assert np.allclose(I.jacobi_scaled_eigenvalues(np.diag([1e-8, 3.0, 1e9])), 1.0)
+
+
+def test_weighted_lowrank_unconstrained_closed_form():
+    """H = H0 + U W U' (section 2.1's quasi-Newton form), no constraints or
+    bounds: x* = -H^-1 p with H assembled explicitly from its definition."""
+    qp = qpgen.bfgs_qp(60, 5, 0, seed=15)
+    qp.lx = np.full(qp.n, -np.inf)
+    qp.ux = np.full(qp.n, np.inf)
+    U = qp.Z.astype(np.float64)
+    H = np.diag(qp.d0) + U @ np.diag(qp.zw) @ U.T
+    res = oracle.ipm_solve(qp)
+    xstar = -np.linalg.solve(H, qp.p)
+    assert res.status == "converged"
+    assert np.max(np.abs(res.x - xstar)) <= 1e-10 * (1 + np.max(np.abs(xstar)))
