@@ -239,6 +239,73 @@ def max_over_ranks(x: float, dist, device: str) -> float:
     return float(t.item())
 
 
+def batch_bytes_per_product(q) -> float:
+    """Algorithmic bytes of one K*v product of a batched dense QP: H (bf16
+    bits or FP64) and A (FP32 or FP64), each read once."""
+    hb = 2.0 if (q.meta or {}).get("H_bf16_bits") is not None else 8.0
+    ab = 4.0 if (q.meta or {}).get("a_f32", False) else 8.0
+    return hb * q.n * q.n + ab * q.m * q.n
+
+
+def batch_line(kq, qps, prec, graph, peak, peak_src, head):
+    """Solve a batch once and describe it: time, convergence, and the
+    effective bandwidth of its products (algorithmic bytes x each QP's PCG
+    iterations / device time of the solve's launches -- the whole replayed
+    iteration in the graph form, so a lower bound there)."""
+    import numpy as np
+    b = kq.qp_create_batch(qps)
+    xs = [np.zeros(q.n) for q in qps]
+    rc, status, st = kq.ipm_solve_batch(b, kq.default_ipm_opts(precision=prec, graph=graph), xs)
+    per = [kq.qp_batch_qp_stats(b, i) for i in range(len(qps))]
+    kq.qp_batch_destroy(b)
+    byts = sum(batch_bytes_per_product(q) * it for q, (_, it) in zip(qps, per))
+    gbs = byts / (st.pcg_kernel_ms * 1e-3) / 1e9 if st.pcg_kernel_ms > 0 else None
+    return dict(head, **{"time_to_1e-6_s": st.time_s, "converged": st.converged,
+                         "status": int(rc), "ipm_iters_max": st.ipm_iters_max,
+                         "pcg_iters": int(st.pcg_iters), "pcg_maxit_hits": st.pcg_maxit_hits,
+                         "device_ms": st.pcg_kernel_ms, "graph_captures": st.graph_captures,
+                         "graph_replays": st.graph_replays,
+                         "sum_n2": int(sum(q.n * q.n for q in qps)),
+                         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                                      "frac": gbs / peak if gbs else None, "peak_source": peak_src,
+                                      "bytes": byts,
+                                      "note": "bf16 H + f32 A per product x each QP's PCG iterations"
+                                              " / device time of the solve"}})
+
+
+def other_configs(kq, qpgen):
+    """Time-to-1e-6 of the other configurations in both forms (one warm-up
+    solve, one timed), for the record next to the benchmark line: c0 (dense
+    n = 200), c2 (linear SVM dual), c4 (dose QP at 1/4 size), and the first
+    32 QPs of the 512-QP batch with n <= 1024 (graph form)."""
+    import numpy as np
+    out = {}
+    for name, mk in (("c0_dense_n200", qpgen.config0), ("c2_svm_50k", qpgen.config2),
+                     ("c4_dose_50k_x_5k", qpgen.config4)):
+        qp = mk()
+        d = {}
+        for prec, form in ((kq.KQ_PREC_F64, "f64"), (kq.KQ_PREC_MIXED, "mixed")):
+            h = kq.create_from(qp, device_tensors=True)
+            x = np.zeros(qp.n)
+            kq.ipm_solve(h, kq.default_ipm_opts(precision=prec), x=x)
+            _, st = kq.ipm_solve(h, kq.default_ipm_opts(precision=prec), x=x)
+            d[form] = {"time_s": st.time_s, "ipm_iters": st.ipm_iters, "pcg_iters": int(st.pcg_iters),
+                       "switched_to_f64": st.switched_to_f64}
+            kq.qp_destroy(h)
+        out[name] = d
+    sizes = qpgen.batch_sizes(512, 64, 4096)
+    ids = [k for k, n in enumerate(sizes) if n <= 1024][:32]
+    qps = [qpgen.batch_qp(k, sizes[k], light=True) for k in ids]
+    peak, peak_src = read_peaks()
+    d = {}
+    for prec, form in ((kq.KQ_PREC_F64, "f64"), (kq.KQ_PREC_MIXED, "mixed")):
+        ln = batch_line(kq, qps, prec, 1, peak, peak_src, {})
+        d[form] = {k: ln[k] for k in ("time_to_1e-6_s", "converged", "pcg_iters", "ipm_iters_max")}
+        d[form]["frac"] = ln["roofline"]["frac"]
+    out["c3_first32_n_le_1024"] = d
+    return out
+
+
 def run_other(args):
     """Time-to-1e-6 of the other configurations, plain FP64 against mixed
     (and batched), on one GPU.  One JSON line per form; the median of
@@ -294,15 +361,12 @@ def run_other(args):
     hi = 1024 if args.workload == "batch128" else 4096
     sizes = qpgen.batch_sizes(nqp, 64, hi, size_seed=5 if args.workload == "batch128" else 0)
     qps = [qpgen.batch_qp(k, n, light=True) for k, n in enumerate(sizes)]
-    for prec, name in ((kq.KQ_PREC_MIXED, "batched mixed"), (kq.KQ_PREC_F64, "batched f64")):
-        b = kq.qp_create_batch(qps)
-        xs = [np.zeros(q.n) for q in qps]
-        rc, status, st = kq.ipm_solve_batch(b, kq.default_ipm_opts(precision=prec), xs)
-        emit({"workload": args.workload, "form": name, "time_to_1e-6_s": st.time_s,
-              "converged": st.converged, "nqp": nqp, "pcg_iters": int(st.pcg_iters),
-              "pcg_maxit_hits": st.pcg_maxit_hits, "pcg_kernel_ms": st.pcg_kernel_ms,
-              "sum_n2": int(sum(n * n for n in sizes))})
-        kq.qp_batch_destroy(b)
+    peak, peak_src = read_peaks()
+    forms = ((kq.KQ_PREC_MIXED, 1, "batched mixed, graph"), (kq.KQ_PREC_F64, 1, "batched f64, graph"),
+             (kq.KQ_PREC_MIXED, 0, "batched mixed, host-driven"))
+    for prec, graph, name in forms:
+        emit(batch_line(kq, qps, prec, graph, peak, peak_src,
+                        {"workload": args.workload, "form": name, "nqp": nqp}))
     if args.sequential:
         tot, its = 0.0, 0
         for q in qps:
@@ -325,6 +389,8 @@ def main():
     ap.add_argument("--pcg-iters", type=int, default=200)
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-others", action="store_true",
+                    help="skip the other configurations' record on the benchmark line")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--workload", default="c1",
                     choices=["c1", "c0", "c2", "c4", "batch128", "batch512"],
@@ -485,6 +551,13 @@ def main():
                "kv_gbs": s3.pcg_products * abytes / (s3.pcg_kernel_ms * 1e-3) / 1e9}
         kq.qp_destroy(h3)
 
+    others = None
+    if rank == 0 and not args.no_others:
+        try:
+            others = other_configs(kq, qpgen)
+        except Exception as e:   # reported, not fatal
+            others = {"error": str(e)[-300:]}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         try:
@@ -524,6 +597,7 @@ def main():
             "gpu_launches": int(sum(s.kernel_launches for s in stats)),
             "clocks": clk.summary(),
             "compare": cmp,
+            "other_configs": others,
             "cpu_baseline": cpu,
         }
         print(json.dumps(line))

@@ -120,6 +120,10 @@ typedef struct {
   int verbose;             /* 1 = one line per IPM iteration on stderr          */
   int record;              /* 1 = keep one kq_ipm_iter per IPM iteration        */
                            /*     (qp_iteration_log); default 0                 */
+  int graph;               /* ipm_solve_batch: 1 = capture the lock-step IPM    */
+                           /*     iteration once in a CUDA graph and replay it, */
+                           /*     every decision taken on the device; 0 = host- */
+                           /*     driven launches (default 1)                   */
 } kq_ipm_opts;
 
 /* One IPM iteration's record (opts.record = 1): the quantities the paper
@@ -322,9 +326,13 @@ typedef struct {
   long long pcg_iters;   /* summed over QPs                                   */
   int pcg_maxit_hits;
   int max_active;
-  double pcg_kernel_ms;  /* device time of the batched PCG launches           */
+  double pcg_kernel_ms;  /* device time of the batched PCG launches (graph:   */
+                         /* of the whole replayed iterations)                 */
   long long pcg_launches;
   double time_s;
+  int graph_captures;    /* opts.graph: captures (one, plus one each time QPs */
+                         /* finished) and replays of the lock-step iteration  */
+  int graph_replays;
 } kq_batch_stats;
 
 /* Create nqp QPs (copies of the inputs, as qp_create) ordered on `stream`. */
@@ -335,6 +343,23 @@ kq_status qp_create_batch(kq_batch *out, int nqp, const kq_qp_desc *descs, void 
 kq_status ipm_solve_batch(kq_batch b, const kq_ipm_opts *opts, double *const *x, int *status,
                           kq_batch_stats *stats);
 kq_status qp_batch_info(kq_batch b, int *nqp, int64_t *n);
+/* QP i's IPM iterations and PCG iterations in the last ipm_solve_batch. */
+kq_status qp_batch_qp_stats(kq_batch b, int i, int *ipm_iters, long long *pcg_iters);
+/* Autotuner support for the batched products (no paper counterpart).
+ * qp_batch_time_product: device time (ms, mean over reps launches after one
+ * warm-up) of one K*v product of QP i alone, on a team of `team` CTAs, in
+ * KQ_PREC_F64 or KQ_PREC_MIXED arithmetic, with the column-blocked A' pass
+ * from n >= colpass_min_n on (0: the current setting).
+ * qp_batch_set_tuning: the table the scheduler then uses, per size bucket
+ * k = floor(log2 n) (k >= nbuckets uses the last): team_cap[k] CTAs at most per
+ * QP and t_prod_us[k] (one product on one CTA) as the QP's cost per iteration;
+ * colpass_min_n as above.  nbuckets = 0 restores the default (cost = bytes per
+ * product, no cap, colpass from n = 512). */
+kq_status qp_batch_time_product(kq_batch b, int i, int team, int precision, int colpass_min_n,
+                                int reps, double *ms);
+kq_status qp_batch_set_tuning(kq_batch b, int nbuckets, const int *team_cap,
+                              const double *t_prod_us, int colpass_min_n);
+
 /* The current iterate of QP i of the batch (after ipm_solve_batch: its final
  * iterate) in original units, as ipm_solve returns it: x (n_i), lam_lA, lam_uA
  * (m_i, zero where the bound is absent), lam_lx, lam_ux (n_i), lam_e (me_i).

@@ -259,8 +259,10 @@ def residual_norm(r: dict) -> float:
 
 
 def infeasibilities(r: dict):
-    """Primal, dual and complementarity infeasibility of section 5.2."""
-    prim = np.sqrt(sum(float(r[k] @ r[k]) for k in ("r_lA", "r_uA", "r_lx", "r_ux")))
+    """Primal, dual and complementarity infeasibility of section 5.2.  The
+    equality residual r_e counts as primal, so the three norms split the
+    residual norm of Eq. (7) exactly: prim^2 + dual^2 + comp^2 = ||r||^2."""
+    prim = np.sqrt(sum(float(r[k] @ r[k]) for k in ("r_e", "r_lA", "r_uA", "r_lx", "r_ux")))
     dual = float(np.linalg.norm(r["r_H"]))
     comp = np.sqrt(sum(float(r[k] @ r[k]) for k in ("r_c1", "r_c2", "r_c3", "r_c4")))
     return prim, dual, comp

@@ -50,7 +50,7 @@ class KqIpmOpts(C.Structure):
                 ("ipm_maxit", C.c_int), ("pcg_tol", C.c_double), ("pcg_maxit", C.c_int),
                 ("precision", C.c_int), ("refine_steps", C.c_int), ("inner_tol", C.c_double),
                 ("timeout_s", C.c_double), ("grid_ctas", C.c_int), ("verbose", C.c_int),
-                ("record", C.c_int)]
+                ("record", C.c_int), ("graph", C.c_int)]
 
 
 class KqIpmIter(C.Structure):
@@ -535,7 +535,7 @@ class KqBatchStats(C.Structure):
                 ("ipm_iters_total", C.c_longlong), ("pcg_iters", C.c_longlong),
                 ("pcg_maxit_hits", C.c_int), ("max_active", C.c_int),
                 ("pcg_kernel_ms", C.c_double), ("pcg_launches", C.c_longlong),
-                ("time_s", C.c_double)]
+                ("time_s", C.c_double), ("graph_captures", C.c_int), ("graph_replays", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -567,6 +567,8 @@ def _batch_lib():
         lib.qp_batch_last_error.argtypes = [P]
         lib.kq_batch_error.restype = C.c_char_p
         lib.kq_batch_error.argtypes = []
+        lib.qp_batch_qp_stats.restype = C.c_int
+        lib.qp_batch_qp_stats.argtypes = [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
         lib.qp_batch_solution.restype = C.c_int
         lib.qp_batch_solution.argtypes = [P, C.c_int] + [P] * 6
         lib._batch_sigs = True
@@ -646,6 +648,16 @@ def qp_batch_solution(batch: Batch, i: int, qp):
     if rc != KQ_OK:
         raise KQError(rc, lib.qp_batch_last_error(batch.b).decode())
     return out
+
+
+def qp_batch_qp_stats(batch: Batch, i: int):
+    """(IPM iterations, PCG iterations) of QP i in the last ipm_solve_batch."""
+    lib = _batch_lib()
+    a, b = C.c_int(), C.c_longlong()
+    rc = lib.qp_batch_qp_stats(batch.b, int(i), C.byref(a), C.byref(b))
+    if rc != KQ_OK:
+        raise KQError(rc, lib.qp_batch_last_error(batch.b).decode())
+    return a.value, b.value
 
 
 def qp_batch_destroy(batch: Batch):

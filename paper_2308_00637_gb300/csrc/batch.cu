@@ -151,6 +151,210 @@ kq_status batch_pcg(kq_batch b, const std::vector<int> &act, const kq_pcg_opts &
   return KQ_OK;
 }
 
+// One lock-step IPM iteration of the batch, enqueued for stream capture:
+// correction passes of the Newton solves (precision, tolerance and stop taken
+// by the control kernels), step recovery, step lengths, update, residuals at
+// the current mu, the mu rule, residuals at the new mu, and the count of QPs
+// still iterating (copied to pinned host memory).  Only QPs active at capture
+// are enqueued; the others stay inactive.
+kq_status enqueue_iteration(kq_batch b, const kq_ipm_opts &o, const kq_pcg_opts &po,
+                            const std::vector<int> &act) {
+  auto &hs = b->qps;
+  BatchPcg &B = b->B;
+  cudaStream_t s = b->stream;
+  std::string e;
+  const int mixed = po.precision == KQ_PREC_MIXED;
+  const int max_passes = (mixed ? po.refine_steps : 0) + 3;
+  batch_graph_pcg_init(B, mixed, s);
+  for (int q : act) {
+    kq_problem *h = hs[q];
+    if (cudaMemsetAsync(h->z, 0, h->nkp * sizeof(double), s) != cudaSuccess ||
+        cudaMemcpyAsync(h->tmp, h->K.rhs, h->nkp * sizeof(double), cudaMemcpyDeviceToDevice, s) != cudaSuccess)
+      return bfail(b, KQ_ERR_CUDA, "batch graph: PCG init");
+  }
+  for (int pass = 0; pass < max_passes; ++pass) {
+    batch_graph_pass_setup(B, pass, po, s);
+    kq_status rc;
+    if ((rc = batch_graph_launch(B, hs[0], 0, s, e)) != KQ_OK) return bfail(b, rc, e);
+    for (int q : act) vec_add_enqueue(hs[q], hs[q]->z, hs[q]->zref);
+    if ((rc = batch_graph_launch(B, hs[0], 2, s, e)) != KQ_OK) return bfail(b, rc, e);
+    for (int q : act) vec_resid_enqueue(hs[q], hs[q]->K.rhs, hs[q]->zref, hs[q]->tmp);
+    batch_graph_pass_finish(B, pass, pass == max_passes - 1, po.maxit, s);
+  }
+  for (int q : act)
+    if (recover_enqueue(hs[q]) != KQ_OK) return bfail(b, KQ_ERR_CUDA, hs[q]->err);
+  batch_graph_step(B, o.gamma, s);
+  for (int q : act)
+    if (update_enqueue(hs[q], 0.0, 0.0) != KQ_OK || assemble_enqueue(hs[q]) != KQ_OK)
+      return bfail(b, KQ_ERR_CUDA, hs[q]->err);
+  batch_graph_mu_rule(B, o.mu0, o.mu_tol, s);
+  for (int q : act)
+    if (assemble_enqueue(hs[q]) != KQ_OK) return bfail(b, KQ_ERR_CUDA, hs[q]->err);
+  batch_graph_count(B, s);
+  if (cudaGetLastError() != cudaSuccess) return bfail(b, KQ_ERR_CUDA, "batch graph: enqueue");
+  return KQ_OK;
+}
+
+void graph_mode(kq_batch b, bool on) {
+  for (size_t q = 0; q < b->qps.size(); ++q) {
+    kq_problem *h = b->qps[q];
+    QpCtl *c = b->B.ctl + q;
+    h->P.gate = on ? &c->active : nullptr;
+    h->P.mu_dev = on ? &c->mu : nullptr;
+    h->P.axal = on ? &c->ax : nullptr;   // ax, al adjacent in QpCtl
+    h->vec_gate = on ? &c->ran : nullptr;
+    h->graph_mode = on;
+  }
+}
+
+// Algorithm 1 over the batch with the lock-step iteration replayed from a
+// CUDA graph; the graph is captured again (teams rebalanced over the QPs
+// still iterating, weighted by their last Newton solve's iterations) only
+// when QPs have finished.
+kq_status ipm_solve_batch_graph_on(kq_batch b, const kq_ipm_opts &o, double *const *x,
+                                   int *status, kq_batch_stats *stats);
+
+// Stream capture needs a stream other than the legacy default stream: when
+// the batch was created on the default stream, the graph path runs on a
+// private non-blocking stream (ordered after the default stream's work) and
+// hands the handles back their stream afterwards.
+kq_status ipm_solve_batch_graph(kq_batch b, const kq_ipm_opts &o, double *const *x, int *status,
+                                kq_batch_stats *stats) {
+  if (b->stream) return ipm_solve_batch_graph_on(b, o, x, status, stats);
+  cudaStream_t ps = nullptr;
+  if (cudaStreamSynchronize(nullptr) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) != cudaSuccess)
+    return bfail(b, KQ_ERR_CUDA, "batch graph: private stream");
+  b->stream = ps;
+  for (kq_problem *h : b->qps) h->stream = ps;
+  const kq_status rc = ipm_solve_batch_graph_on(b, o, x, status, stats);
+  cudaStreamSynchronize(ps);
+  b->stream = nullptr;
+  for (kq_problem *h : b->qps) h->stream = nullptr;
+  cudaStreamDestroy(ps);
+  return rc;
+}
+
+kq_status ipm_solve_batch_graph_on(kq_batch b, const kq_ipm_opts &o, double *const *x,
+                                   int *status, kq_batch_stats *stats) {
+  auto t0 = std::chrono::steady_clock::now();
+  auto &hs = b->qps;
+  BatchPcg &B = b->B;
+  const int nq = (int)hs.size();
+  cudaStream_t s = b->stream;
+  kq_pcg_opts po;
+  po.tol = o.pcg_tol; po.maxit = o.pcg_maxit; po.precision = o.precision;
+  po.refine_steps = o.refine_steps; po.inner_tol = o.inner_tol;
+  kq_batch_stats st{};
+  for (kq_problem *h : hs) {
+    h->timeout_s = o.timeout_s > 0 ? o.timeout_s : 2.0;
+    h->solved = false;
+    h->state_set = false;
+    h->mu = o.mu0;
+    if (init_state(h) != KQ_OK || assemble_enqueue(h) != KQ_OK) return bfail(b, KQ_ERR_CUDA, h->err);
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return bfail(b, KQ_ERR_CUDA, "batch init");
+  double n2;
+  for (kq_problem *h : hs) assemble_finish(h, &n2, nullptr);
+  std::vector<double> weight(nq, 1.0);
+  std::string e;
+  kq_status rc = batch_graph_prepare(B, hs, weight, e);   // allocates the control words
+  if (rc != KQ_OK) return bfail(b, rc, e);
+  std::vector<QpCtl> ctl(nq);
+  for (QpCtl &c : ctl) {
+    c = QpCtl{};
+    c.active = 1;
+    c.mu = o.mu0;
+    c.status = KQ_ERR_IPM_MAXIT;
+  }
+  if (cudaMemcpy(B.ctl, ctl.data(), nq * sizeof(QpCtl), cudaMemcpyHostToDevice) != cudaSuccess)
+    return bfail(b, KQ_ERR_CUDA, "batch graph: control words");
+  graph_mode(b, true);
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int captured = nq, it = 0, count = nq;
+  double ms_total = 0.0;
+  kq_status out = KQ_OK;
+  for (it = 1; it <= o.ipm_maxit; ++it) {
+    if (!exec) {
+      std::vector<int> act;
+      for (int q = 0; q < nq; ++q)
+        if (weight[q] > 0.0) act.push_back(q);
+      if ((rc = batch_graph_prepare(B, hs, weight, e)) != KQ_OK) { out = bfail(b, rc, e); break; }
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        out = bfail(b, KQ_ERR_CUDA, "batch graph: begin capture");
+        break;
+      }
+      rc = enqueue_iteration(b, o, po, act);
+      const cudaError_t ce = cudaStreamEndCapture(s, &graph);
+      if (rc != KQ_OK) { out = rc; break; }
+      if (ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+        out = bfail(b, KQ_ERR_CUDA, std::string("batch graph: capture: ") + cudaGetErrorString(ce));
+        break;
+      }
+      st.graph_captures++;
+      captured = (int)act.size();
+    }
+    cudaEventRecord(B.ev0, s);
+    if (cudaGraphLaunch(exec, s) != cudaSuccess) { out = bfail(b, KQ_ERR_CUDA, "batch graph: launch"); break; }
+    cudaEventRecord(B.ev1, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) { out = bfail(b, KQ_ERR_CUDA, "batch graph: replay"); break; }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, B.ev0, B.ev1);
+    ms_total += ms;
+    st.graph_replays++;
+    count = *B.h_count;
+    if (o.verbose) {
+      fprintf(stderr, "batch graph ipm %3d active %4d replay %.1f ms\n", it, count, ms);
+      fflush(stderr);
+    }
+    if (count == 0) break;
+    if (count < captured) {
+      // QPs finished: rebalance the teams over the others at the next capture
+      if (cudaMemcpy(ctl.data(), B.ctl, nq * sizeof(QpCtl), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        out = bfail(b, KQ_ERR_CUDA, "batch graph: control read-back");
+        break;
+      }
+      for (int q = 0; q < nq; ++q) weight[q] = ctl[q].active ? std::max(1, ctl[q].used) : 0.0;
+      cudaGraphExecDestroy(exec);
+      cudaGraphDestroy(graph);
+      exec = nullptr;
+      graph = nullptr;
+    }
+  }
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  graph_mode(b, false);
+  if (out != KQ_OK) return out;
+  if (cudaMemcpy(ctl.data(), B.ctl, nq * sizeof(QpCtl), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return bfail(b, KQ_ERR_CUDA, "batch graph: control read-back");
+  for (int q = 0; q < nq; ++q) {
+    const QpCtl &c = ctl[q];
+    if (x && x[q]) outputs_enqueue(hs[q], x[q], nullptr, nullptr, nullptr, nullptr, nullptr);
+    if (status) status[q] = c.status;
+    hs[q]->mu = c.mu;
+    hs[q]->solved = c.status == KQ_OK;
+    hs[q]->batch_pcg_iters = c.pcg_iters;
+    hs[q]->batch_ipm_iters = c.ipm_iters;
+    hs[q]->kkt_valid = false;
+    st.ipm_iters_max = std::max(st.ipm_iters_max, c.ipm_iters);
+    st.ipm_iters_total += c.ipm_iters;
+    st.pcg_iters += c.pcg_iters;
+    st.pcg_maxit_hits += c.maxit_hits;
+    if (c.status == KQ_OK) st.converged++;
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess) return bfail(b, KQ_ERR_CUDA, "batch outputs");
+  st.max_active = nq;
+  st.pcg_kernel_ms = ms_total;
+  st.pcg_launches = B.launches;
+  st.time_s = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
+  for (int q = 0; q < nq; ++q)
+    if (ctl[q].status != KQ_OK && ctl[q].status != KQ_ERR_IPM_MAXIT)
+      return bfail(b, ctl[q].status, "QP " + std::to_string(q) + " failed");
+  return st.converged == nq ? KQ_OK : KQ_ERR_IPM_MAXIT;
+}
+
 }  // namespace
 
 extern "C" {
@@ -210,6 +414,63 @@ kq_status qp_batch_solution(kq_batch b, int i, double *x, double *lam_lA, double
   return KQ_OK;
 }
 
+kq_status qp_batch_time_product(kq_batch b, int i, int team, int precision, int colpass_min_n,
+                                int reps, double *ms) {
+  if (!b) return bfail(nullptr, KQ_ERR_ARG, "null batch");
+  if (i < 0 || i >= (int)b->qps.size() || team < 1 || reps < 1 || !ms)
+    return bfail(b, KQ_ERR_ARG, "qp_batch_time_product: bad arguments");
+  kq_problem *h = b->qps[i];
+  if (!h->kkt_valid && kkt_assemble(h) != KQ_OK) return bfail(b, KQ_ERR_CUDA, h->err);
+  BatchTune saved = b->B.tune;
+  b->B.tune.force_team = team;
+  if (colpass_min_n > 0) b->B.tune.colpass_min_n = colpass_min_n;
+  std::vector<kq_problem *> hs(b->qps.begin(), b->qps.end());
+  std::vector<int> idx{i};
+  std::vector<const double *> in{h->z};     // NKP entries, finite (zero or a direction)
+  std::vector<double *> out{h->zref};
+  std::vector<double> tol{0.0};
+  std::vector<int> mx{0}, its, errs;
+  std::vector<double> rr, bb;
+  double total = 0.0;
+  kq_status rc = KQ_OK;
+  std::string e;
+  for (int r = 0; r <= reps && rc == KQ_OK; ++r) {
+    float t = 0.f;
+    rc = batch_pcg_launch(b->B, hs, idx, in, out, tol, mx, 1,
+                          precision == KQ_PREC_MIXED ? KQ_PREC_MIXED : KQ_PREC_F64, b->stream,
+                          its, errs, rr, bb, &t, e);
+    if (r > 0) total += t;   // the first launch warms up
+  }
+  b->B.tune = saved;
+  if (rc != KQ_OK) return bfail(b, rc, e);
+  *ms = total / reps;
+  return KQ_OK;
+}
+
+kq_status qp_batch_set_tuning(kq_batch b, int nbuckets, const int *team_cap,
+                              const double *t_prod_us, int colpass_min_n) {
+  if (!b) return bfail(nullptr, KQ_ERR_ARG, "null batch");
+  if (nbuckets < 0 || nbuckets > 40 || (nbuckets > 0 && (!team_cap || !t_prod_us)))
+    return bfail(b, KQ_ERR_ARG, "qp_batch_set_tuning: bad table");
+  BatchTune t;
+  for (int k = 0; k < nbuckets; ++k) {
+    if (team_cap[k] < 1 || !(t_prod_us[k] > 0.0)) return bfail(b, KQ_ERR_ARG, "qp_batch_set_tuning: bad entry");
+    t.team_cap.push_back(team_cap[k]);
+    t.t_prod_us.push_back(t_prod_us[k]);
+  }
+  t.colpass_min_n = colpass_min_n > 0 ? colpass_min_n : 512;
+  b->B.tune = t;
+  return KQ_OK;
+}
+
+kq_status qp_batch_qp_stats(kq_batch b, int i, int *ipm_iters, long long *pcg_iters) {
+  if (!b) return bfail(nullptr, KQ_ERR_ARG, "null batch");
+  if (i < 0 || i >= (int)b->qps.size()) return bfail(b, KQ_ERR_ARG, "QP index out of range");
+  if (ipm_iters) *ipm_iters = b->qps[i]->batch_ipm_iters;
+  if (pcg_iters) *pcg_iters = b->qps[i]->batch_pcg_iters;
+  return KQ_OK;
+}
+
 kq_status qp_batch_info(kq_batch b, int *nqp, int64_t *n) {
   if (!b) return bfail(nullptr, KQ_ERR_ARG, "null batch");
   if (nqp) *nqp = (int)b->qps.size();
@@ -225,6 +486,7 @@ kq_status ipm_solve_batch(kq_batch b, const kq_ipm_opts *opts, double *const *x,
   kq_ipm_opts o;
   kq_default_ipm_opts(&o);
   if (opts) o = *opts;
+  if (o.graph) return ipm_solve_batch_graph(b, o, x, status, stats);
   kq_pcg_opts po;
   po.tol = o.pcg_tol; po.maxit = o.pcg_maxit; po.precision = o.precision;
   po.refine_steps = o.refine_steps; po.inner_tol = o.inner_tol;
@@ -239,6 +501,7 @@ kq_status ipm_solve_batch(kq_batch b, const kq_ipm_opts *opts, double *const *x,
     h->solved = false;
     h->state_set = false;
     h->mu = o.mu0;
+    h->batch_pcg_iters = 0;
     if (init_state(h) != KQ_OK || assemble_enqueue(h) != KQ_OK) return bfail(b, KQ_ERR_CUDA, h->err);
   }
   if (cudaStreamSynchronize(s) != cudaSuccess) return bfail(b, KQ_ERR_CUDA, "batch init");
@@ -259,6 +522,7 @@ kq_status ipm_solve_batch(kq_batch b, const kq_ipm_opts *opts, double *const *x,
     if (rc != KQ_OK) return rc;
     long long its_sum = 0;
     for (size_t j = 0; j < act.size(); ++j) {
+      hs[act[j]]->batch_pcg_iters += pits[j];
       st.pcg_iters += pits[j];
       st.pcg_maxit_hits += hit[j];
       last_iters[act[j]] = (double)std::max<long long>(1, pits[j]);
@@ -309,6 +573,7 @@ kq_status ipm_solve_batch(kq_batch b, const kq_ipm_opts *opts, double *const *x,
   for (int i = 0; i < nq; ++i) {
     if (x && x[i]) outputs_enqueue(hs[i], x[i], nullptr, nullptr, nullptr, nullptr, nullptr);
     if (status) status[i] = stat[i];
+    hs[i]->batch_ipm_iters = iters[i];
     st.ipm_iters_max = std::max(st.ipm_iters_max, iters[i]);
     st.ipm_iters_total += iters[i];
     if (stat[i] == KQ_OK) st.converged++;

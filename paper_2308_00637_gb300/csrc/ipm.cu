@@ -19,6 +19,9 @@
 
 namespace {
 
+// batched solver's captured graph: a kernel of a QP that has stopped iterating returns at once
+#define KQ_GATE(P) \
+  if ((P).gate && *(P).gate == 0) return
 constexpr int NB = 256;      // blocks of the grid-stride IPM kernels
 constexpr int NT = 256;
 thread_local std::string g_global_err;
@@ -224,6 +227,7 @@ __global__ void k_init_rows(DevProb P, DevState S, const double *t) {
 // t_a = rho_a A_a v  (all general rows),  tC_e = C_e v
 template <class AS>
 __global__ void k_rowdot_dense(DevProb P, const double *v, double *t, double *tC) {
+  KQ_GATE(P);
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -244,6 +248,7 @@ __global__ void k_rowdot_dense(DevProb P, const double *v, double *t, double *tC
 }
 
 __global__ void k_rowdot_prows(DevProb P, const double *v, double *t, double *tC) {
+  KQ_GATE(P);
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -266,6 +271,7 @@ __global__ void k_rowdot_prows(DevProb P, const double *v, double *t, double *tC
 // t_a = rho_a A_a v for the rows of a CSR A, tC_e = C_e v
 template <class AS>
 __global__ void k_rowdot_acsr(DevProb P, const double *v, double *t, double *tC) {
+  KQ_GATE(P);
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -302,6 +308,7 @@ __global__ void k_csr_rowdot(DevProb P, const double *v, double *y) {
 // hx = sigma H v (DENSE)
 template <class HS>
 __global__ void k_hx_dense(DevProb P, const double *v, double *hx) {
+  KQ_GATE(P);
   const int lane = threadIdx.x & 31;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t W = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -356,8 +363,9 @@ struct RowCoef { double *c1, *c2, *c3; };
 
 __global__ void k_rows_resid(DevProb P, DevState S, DevKKT K, const double *t, const double *tC,
                              RowCoef cf, double *part) {
+  KQ_GATE(P);
   __shared__ double sh[32 * 2];
-  const double mu = K.mu;
+  const double mu = P.mu_dev ? *P.mu_dev : K.mu;
   double ss[2] = {0.0, 0.0};   // [primal (row and equality residuals), complementarity]
   const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
   for (int64_t a = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; a < P.m; a += (int64_t)gridDim.x * blockDim.x) {
@@ -415,6 +423,7 @@ __global__ void k_rows_resid(DevProb P, DevState S, DevKKT K, const double *t, c
 // thread per column j:  acc_k[j] = sum_rows c_k(row) * row_j (^2 for k = 3)
 template <class AS>
 __global__ void k_rows_scatter_dense(DevProb P, RowCoef cf, double *acc1, double *acc2, double *acc3) {
+  KQ_GATE(P);
   const AS *A = reinterpret_cast<const AS *>(P.Ad);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < P.n; j += (int64_t)gridDim.x * blockDim.x) {
     double s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -475,8 +484,9 @@ __global__ void k_csr_scatter(DevProb P, const double *y, RowCoef cf, double *ac
 // x part: r_H, bound residuals, r1, rhs_x = r1 + acc2, diag_x = hdiag + dg + acc3
 __global__ void k_x_resid(DevProb P, DevState S, DevKKT K, const double *hx, const double *acc1,
                           const double *acc2, const double *acc3, double *part) {
+  KQ_GATE(P);
   __shared__ double sh[32 * 3];
-  const double mu = K.mu;
+  const double mu = P.mu_dev ? *P.mu_dev : K.mu;
   double ss[3] = {0.0, 0.0, 0.0};   // [bound residuals, r_H, bound complementarity]
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n; i += (int64_t)gridDim.x * blockDim.x) {
     const bool fl = P.haslx[i], fu = P.hasux[i];
@@ -507,6 +517,7 @@ __global__ void k_x_resid(DevProb P, DevState S, DevKKT K, const double *hx, con
 __global__ void k_recover_ratio(DevProb P, DevState S, DevKKT K, const double *z, const double *t,
                                 double *dsl, double *dsu, double *dslx, double *dsux,
                                 double *dllx, double *dlux, double *part) {
+  KQ_GATE(P);
   __shared__ double sh[32];
   double ax = INFINITY, al = INFINITY;
   const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
@@ -549,6 +560,8 @@ __global__ void k_recover_ratio(DevProb P, DevState S, DevKKT K, const double *z
 __global__ void k_update(DevProb P, DevState S, const double *z, const double *dsl, const double *dsu,
                          const double *dslx, const double *dsux, const double *dllx,
                          const double *dlux, double ax, double al) {
+  KQ_GATE(P);
+  if (P.axal) { ax = P.axal[0]; al = P.axal[1]; }
   const int64_t lo_off = P.n + P.me, up_off = P.n + P.me + P.m;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < P.n; i += (int64_t)gridDim.x * blockDim.x) {
     S.x[i] += ax * z[i];
@@ -563,7 +576,9 @@ __global__ void k_update(DevProb P, DevState S, const double *z, const double *d
     S.le[e] += al * z[P.n + e];
 }
 
-__global__ void k_reduce_cols(int nb, int ncol, const double *part, int min_mask, double *out) {
+__global__ void k_reduce_cols(int nb, int ncol, const double *part, int min_mask, double *out,
+                              const int *gate) {
+  if (gate && *gate == 0) return;
   __shared__ double sh[32];
   for (int c = 0; c < ncol; ++c) {
     if ((min_mask >> c) & 1) {
@@ -690,10 +705,12 @@ kq_status hx_apply(kq_problem *h, const double *v, double *hx) {
 // Reduce ncols columns of block partials (sum, or min where bit c of min_mask
 // is set) into h->h_red[off .. off+ncols) asynchronously (no host sync).
 kq_status reduce_async(kq_problem *h, int ncols, int min_mask, int off) {
-  k_reduce_cols<<<1, 256, 0, h->stream>>>(NB, ncols, h->red, min_mask, h->red_out + off);
+  k_reduce_cols<<<1, 256, 0, h->stream>>>(NB, ncols, h->red, min_mask, h->red_out + off,
+                                           h->P.gate);
   ++h->launches;
-  KQ_CUDA(h, cudaMemcpyAsync(h->h_red + off, h->red_out + off, ncols * sizeof(double),
-                             cudaMemcpyDeviceToHost, h->stream));
+  if (!h->graph_mode)   // in a captured graph the results stay on the device
+    KQ_CUDA(h, cudaMemcpyAsync(h->h_red + off, h->red_out + off, ncols * sizeof(double),
+                               cudaMemcpyDeviceToHost, h->stream));
   return KQ_OK;
 }
 
@@ -837,11 +854,14 @@ kq_status outputs_enqueue(kq_problem *h, double *x, double *lam_lA, double *lam_
 }
 
 // small vector helpers used by the batched solver
-__global__ void k_vec_add(int64_t N, double *z, const double *dz) {
+__global__ void k_vec_add(int64_t N, double *z, const double *dz, const int *gate) {
+  if (gate && *gate == 0) return;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
     z[i] += dz[i];
 }
-__global__ void k_vec_resid(int64_t N, const double *rhs, const double *kz, double *res, double *part) {
+__global__ void k_vec_resid(int64_t N, const double *rhs, const double *kz, double *res, double *part,
+                            const int *gate) {
+  if (gate && *gate == 0) return;
   __shared__ double sh[32];
   double s[1] = {0.0};
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
@@ -854,7 +874,7 @@ __global__ void k_vec_resid(int64_t N, const double *rhs, const double *kz, doub
 }
 kq_status vec_add_enqueue(kq_problem *h, double *z, const double *dz) {
   const int nb = (int)std::min<int64_t>(NB, ceil_div64(h->nkp, NT));
-  k_vec_add<<<nb, NT, 0, h->stream>>>(h->nkp, z, dz);
+  k_vec_add<<<nb, NT, 0, h->stream>>>(h->nkp, z, dz, h->vec_gate);
   ++h->launches;
   return KQ_OK;
 }
@@ -862,7 +882,7 @@ kq_status vec_add_enqueue(kq_problem *h, double *z, const double *dz) {
 kq_status vec_resid_enqueue(kq_problem *h, const double *rhs, const double *kz, double *res) {
   KQ_CUDA(h, cudaMemsetAsync(h->red, 0, NB * sizeof(double), h->stream));
   const int nb = (int)std::min<int64_t>(NB, ceil_div64(h->nkp, NT));
-  k_vec_resid<<<nb, NT, 0, h->stream>>>(h->nkp, rhs, kz, res, h->red);
+  k_vec_resid<<<nb, NT, 0, h->stream>>>(h->nkp, rhs, kz, res, h->red, h->vec_gate);
   ++h->launches;
   return reduce_async(h, 1, 0, 8);
 }
@@ -891,6 +911,7 @@ void kq_default_ipm_opts(kq_ipm_opts *o) {
   o->grid_ctas = 0;
   o->verbose = 0;
   o->record = 0;
+  o->graph = 1;
 }
 
 void kq_default_pcg_opts(kq_pcg_opts *o) {

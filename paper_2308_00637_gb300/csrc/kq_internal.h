@@ -48,6 +48,29 @@ struct DevProb {
   const double *lx = nullptr, *ux = nullptr;
   const uint8_t *haslx = nullptr, *hasux = nullptr;
   const double *hdiag = nullptr;     // diag(H) scaled (zeros for CSR_LSQ: added in pass)
+  // device-side control (the batched solver's captured graph): when set, the
+  // IPM kernels return at once unless *gate != 0, mu is read from *mu_dev and
+  // the step lengths from axal[0..1]
+  const int *gate = nullptr;
+  const double *mu_dev = nullptr;
+  const double *axal = nullptr;
+};
+
+// Per-QP state of the batched solver's device-side control (captured graph).
+struct QpCtl {
+  int active;        // Algorithm 1 still iterating (gate of the IPM kernels)
+  int ran;           // ran a PCG pass in the current pass (gate of its follow-up)
+  int pcg_done;      // the current Newton solve has finished
+  int fp32_ok;       // FP32 correction passes still pay for this QP
+  int used;          // PCG iterations of the current Newton solve
+  int kexp;          // mu = mu0 10^-kexp
+  int ipm_iters;
+  int status;        // KQ_OK once converged; an error code if a step failed
+  int maxit_hits;    // Newton solves stopped at the iteration cap
+  int prec;          // precision of the current pass
+  long long pcg_iters;
+  double mu, bnorm, resn, resn_before, tol_rel;
+  double ax, al;     // step lengths of the current iteration (Eq. (10))
 };
 
 // Device state of the iterate (scaled units).
@@ -210,6 +233,13 @@ struct kq_problem {
   int lz_steps = 0;             // Lanczos estimates of the last recorded pass
   double lz_min = 0.0, lz_max = 0.0;
   std::vector<kq_ipm_iter> iter_log;
+  // batched solver's captured graph: reductions stay on the device, and the
+  // vector helpers of a correction pass run only when *vec_gate != 0
+  bool graph_mode = false;
+  const int *vec_gate = nullptr;
+  // batched solver: this QP's totals over the last ipm_solve_batch
+  long long batch_pcg_iters = 0;
+  int batch_ipm_iters = 0;
 };
 
 // ---------------------------------------------------------------- host helpers
@@ -245,8 +275,30 @@ kq_status pcg_dense_raw(const DevProb &P, const double *Dl, const double *Du, co
                         double *bb, std::string *msg);
 
 // batched dense PCG (pcg.cu)
+// Tuning of the batched dense products (the autotuner's table, per size
+// bucket floor(log2 n)): measured time of one K*v product on one CTA (the
+// scheduler's cost), the team size beyond which it stops paying, and the n
+// from which the A' part runs as the column-blocked second pass.
+struct BatchTune {
+  std::vector<int> team_cap;
+  std::vector<double> t_prod_us;
+  int colpass_min_n = 512;
+  int force_team = 0;          // timing runs: the team size of the single problem
+};
+
 struct BatchPcg {
   int nqp = 0, G = 0, max_n = 0;
+  BatchTune tune;
+  // captured-graph path: three argument arrays (FP32 solve, FP64 solve, FP64
+  // apply), per-QP control, status words of the three launch kinds
+  unsigned char *gargs = nullptr;
+  QpCtl *ctl = nullptr;
+  double **redout = nullptr;       // per QP: its handle's reduction results
+  int *g_iters = nullptr, *g_err = nullptr;
+  double *g_resn = nullptr;
+  int *d_count = nullptr, *h_count = nullptr;
+  int gblocks = 0;
+  size_t gsmem[3] = {0, 0, 0};
   std::vector<void *> allocs;
   unsigned char *args = nullptr, *teams = nullptr;
   int *cta_team = nullptr, *team_qps = nullptr;
@@ -265,6 +317,20 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
                            std::vector<int> &iters, std::vector<int> &errs,
                            std::vector<double> &rr, std::vector<double> &bb, float *ms,
                            std::string &err, const std::vector<double> *weight = nullptr);
+
+// captured-graph path of the batched solver (pcg.cu): per-QP argument arrays
+// and teams over the problems with weight > 0, the three kinds of batched
+// launch, and the device-side control kernels (QpCtl)
+kq_status batch_graph_prepare(BatchPcg &B, const std::vector<kq_problem *> &hs,
+                              const std::vector<double> &weight, std::string &err);
+kq_status batch_graph_launch(BatchPcg &B, const kq_problem *h0, int which, cudaStream_t s,
+                             std::string &err);
+void batch_graph_pcg_init(BatchPcg &B, int mixed, cudaStream_t s);
+void batch_graph_pass_setup(BatchPcg &B, int pass, const kq_pcg_opts &o, cudaStream_t s);
+void batch_graph_pass_finish(BatchPcg &B, int pass, int last, int maxit, cudaStream_t s);
+void batch_graph_step(BatchPcg &B, double gamma, cudaStream_t s);
+void batch_graph_mu_rule(BatchPcg &B, double mu0, double mu_tol, cudaStream_t s);
+void batch_graph_count(BatchPcg &B, cudaStream_t s);
 
 // ipm kernels (ipm.cu)
 kq_status kkt_assemble(kq_problem *h);   // residuals, rhs, D, diag at state & mu

@@ -70,7 +70,12 @@ struct PcgArgs {
   float *p32_0, *p32_1, *y32;   // FP32 copies of p (paired with pb0 / pb1) and y (or null)
   double *lanczos;              // (alpha_j, beta_j) per iteration, or null (not recorded)
   int lanczos_cap;              // iterations that fit in lanczos
+  int run;                      // batched launches: 0 = skip this problem
+  int colpass_min_n;            // dense: column-blocked A' pass from this n on (0: 512)
 };
+
+// barrier parameter of the problem (device-side in the batched solver's graph)
+__device__ __forceinline__ double mu_of(const PcgArgs &a) { return a.P.mu_dev ? *a.P.mu_dev : a.mu; }
 
 __device__ __forceinline__ double ldcg(const double *p) { return __ldcg(p); }
 
@@ -269,7 +274,8 @@ struct OpDense {
     const bool avec = (ald % 8 == 0) && ((reinterpret_cast<uintptr_t>(Ad) & 15) == 0);
     // general rows handled here only when A is dense (a CSR A has its own pass)
     const int64_t md = P.akind == KQ_A_DENSE ? m : 0;
-    const bool colpass = n >= 512 && md > 0 && a.coefA != nullptr && avec;
+    const bool colpass = n >= (a.colpass_min_n > 0 ? a.colpass_min_n : 512) && md > 0 &&
+                         a.coefA != nullptr && avec;
     double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
     for (int64_t j = tid; j < npad; j += blockDim.x) {
       pw[j] = j < n ? (T)(ldcg(ysrc + j) + beta * ldcg(pold + j)) : (T)0;
@@ -345,11 +351,11 @@ struct OpDense {
       dot = warp_sum(dot);
       const double t = (double)dot;
       const double pe = ldcg(ysrc + n + e) + beta * ldcg(pold + n + e);
-      const double coef = 2.0 * t / a.mu + pe;
+      const double coef = 2.0 * t / mu_of(a) + pe;
       const T cf = (T)coef;
       for (int64_t j = lane; j < n; j += 32) atomicAdd(acc + j, cf * (T)cr[j]);
       if (lane == 0) {
-        const double qe = t + a.mu * pe;
+        const double qe = t + mu_of(a) * pe;
         a.qlam[e] = qe;
         pq += coef * t + pe * qe;
       }
@@ -434,9 +440,9 @@ struct OpLowrank {
     for (int64_t e = tid; e < me; e += blockDim.x) {
       const double t = __ldcg(a.g + k + e);
       const double pe = ldcg(ysrc + n + e) + beta * ldcg(pold + n + e);
-      cf[e] = 2.0 * t / a.mu + pe;
+      cf[e] = 2.0 * t / mu_of(a) + pe;
       if (cta == 0) {
-        const double qe = t + a.mu * pe;
+        const double qe = t + mu_of(a) * pe;
         a.qlam[e] = qe;
         pq += pe * qe;
       }
@@ -1322,14 +1328,14 @@ __device__ double csr_a_rows(const PcgArgs &a, const double *ysrc, const double 
       dot = warp_sum(dot);
       const double t = (double)dot;
       const double pe = ldcg(ysrc + n + e) + beta * ldcg(pold + n + e);
-      const double coef = 2.0 * t / a.mu + pe;
+      const double coef = 2.0 * t / mu_of(a) + pe;
       const T cf = (T)coef;
       for (int64_t j = lane; j < n; j += 32) {
         const T v = cf * (T)cr[j];
         if (v != (T)0) atomicAdd(accg + j, v);
       }
       if (lane == 0) {
-        const double qe = t + a.mu * pe;
+        const double qe = t + mu_of(a) * pe;
         a.qlam[e] = qe;
         pq += coef * t + pe * qe;
       }
@@ -1631,7 +1637,32 @@ __global__ void __launch_bounds__(512, 1) pcg_batch_kernel(const PcgArgs *__rest
   const TeamInfo ti = teams[cta_team[blockIdx.x]];
   const int rank = blockIdx.x - ti.first_cta;
   for (int q = ti.qp_begin; q < ti.qp_end; ++q) {
-    pcg_body<OpDense<HS, AS>, T>(args[team_qps[q]], rank, ti.size, smem, sh, sbuf);
+    const PcgArgs &aq = args[team_qps[q]];
+    if (!aq.run) continue;          // uniform over the team: written before the launch
+    pcg_body<OpDense<HS, AS>, T>(aq, rank, ti.size, smem, sh, sbuf);
+    __syncthreads();
+  }
+}
+
+// The captured graph's correction pass: one launch in which each problem's
+// team runs it in the precision its control word chose (FP32 arguments in
+// args32, FP64 in args64; run flags set on the device before the launch).
+template <class HS, class AS>
+__global__ void __launch_bounds__(512, 1) pcg_batch_kernel_dual(const PcgArgs *__restrict__ args32,
+                                                                 const PcgArgs *__restrict__ args64,
+                                                                 const int *__restrict__ cta_team,
+                                                                 const TeamInfo *__restrict__ teams,
+                                                                 const int *__restrict__ team_qps) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double sh[32 * 2];
+  __shared__ double sbuf[512];
+  const TeamInfo ti = teams[cta_team[blockIdx.x]];
+  const int rank = blockIdx.x - ti.first_cta;
+  for (int q = ti.qp_begin; q < ti.qp_end; ++q) {
+    const int j = team_qps[q];
+    if (args32[j].run) pcg_body<OpDense<HS, AS>, float>(args32[j], rank, ti.size, smem, sh, sbuf);
+    else if (args64[j].run) pcg_body<OpDense<HS, AS>, double>(args64[j], rank, ti.size, smem, sh, sbuf);
+    else continue;
     __syncthreads();
   }
 }
@@ -1911,20 +1942,28 @@ void batch_pcg_free(BatchPcg &B) {
   B.ev0 = B.ev1 = nullptr;
 }
 
-// One launch: PCG solves (apply = 0) or single K*v products (apply = 1) of the
-// listed problems.  Teams: problems whose share of the total cost is worth
-// two or more CTAs get their own team of that size; the rest are packed onto
-// single-CTA teams, largest first onto the least-loaded team.
-kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
-                           const std::vector<int> &idx, const std::vector<const double *> &rhs,
-                           const std::vector<double *> &out, const std::vector<double> &tol,
-                           const std::vector<int> &maxit, int apply, int prec, cudaStream_t s,
-                           std::vector<int> &iters, std::vector<int> &errs,
-                           std::vector<double> &rr, std::vector<double> &bb, float *ms,
-                           std::string &err, const std::vector<double> *weight) {
+// Teams of CTAs for one batched launch over the listed problems: a problem
+// whose share of the total cost (bytes per product times its expected
+// products) is worth two or more CTAs gets a team of that size; the rest are
+// packed onto single-CTA teams, largest first onto the least-loaded team.
+struct TeamPlan {
+  std::vector<TeamInfo> teams;
+  std::vector<int> cta_team, team_qps, team_of;
+  int nblocks = 0;
+};
+
+int size_bucket(int64_t n, int nb) {
+  int b = 0;
+  while ((int64_t(2) << b) <= n && b + 1 < nb) ++b;
+  return b;
+}
+
+TeamPlan plan_teams(int G, const std::vector<kq_problem *> &hs, const std::vector<int> &idx,
+                    const std::vector<double> *weight, const BatchTune *tune = nullptr) {
   const int k = (int)idx.size();
-  iters.assign(k, 0); errs.assign(k, 0); rr.assign(k, 0.0); bb.assign(k, 0.0);
-  if (k == 0) { if (ms) *ms = 0.f; return KQ_OK; }
+  TeamPlan tp;
+  const bool tuned = tune && !tune->t_prod_us.empty();
+  const int nb = tuned ? (int)tune->t_prod_us.size() : 0;
   // ---- costs: bytes per product times the expected number of products
   std::vector<double> cost(k);
   double total = 0.0;
@@ -1932,8 +1971,10 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
     const kq_problem *h = hs[idx[j]];
     const double hb = h->P.hdtype == KQ_F64 ? 8.0 : (h->P.hdtype == KQ_F32 ? 4.0 : 2.0);
     const double ab = h->P.adtype == KQ_F64 ? 8.0 : 4.0;
-    cost[j] = (hb * h->n * h->n + ab * h->m * h->n + 64.0 * h->nkp) *
-              (weight ? std::max(1.0, (*weight)[j]) : 1.0);
+    // measured time of one product (autotuner) or its bytes
+    const double per = tuned ? tune->t_prod_us[size_bucket(h->n, nb)]
+                             : hb * h->n * h->n + ab * h->m * h->n + 64.0 * h->nkp;
+    cost[j] = per * (weight ? std::max(1.0, (*weight)[j]) : 1.0);
     total += cost[j];
   }
   std::vector<int> order(k);
@@ -1942,7 +1983,6 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
   std::vector<TeamInfo> teams;
   std::vector<std::vector<int>> members;
   int used = 0;
-  const int G = B.G;
   size_t q = 0;
   for (; q < order.size(); ++q) {
     const int j = order[q];
@@ -1951,6 +1991,8 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
     const kq_problem *hj = hs[idx[j]];
     t = (int)std::min<int64_t>(t, ceil_div64(hj->n + hj->m + hj->me, 32));
     t = std::min(t, hj->num_sms);     // the problem's slot buffer holds up to num_sms CTAs
+    if (tuned) t = std::min(t, tune->team_cap[size_bucket(hj->n, nb)]);
+    if (tune && tune->force_team > 0 && k == 1) t = std::min(tune->force_team, hj->num_sms);
     // keep one CTA for the problems packed onto single CTAs, unless none is
     // left to pack; a team that does not fit is shrunk, not dropped (a
     // dropped problem would run on one CTA)
@@ -1976,18 +2018,43 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
     members[first_single + best].push_back(j);
   }
   const int nblocks = used + nsingle;
-  std::vector<int> cta_team(nblocks), team_qps;
+  std::vector<int> &cta_team = tp.cta_team, &team_qps = tp.team_qps;
+  cta_team.assign(nblocks, 0);
   for (size_t t = 0; t < teams.size(); ++t) {
     teams[t].qp_begin = (int)team_qps.size();
     for (int j : members[t]) team_qps.push_back(j);
     teams[t].qp_end = (int)team_qps.size();
     for (int c = 0; c < teams[t].size; ++c) cta_team[teams[t].first_cta + c] = (int)t;
   }
+  tp.team_of.assign(k, 0);
+  for (size_t t = 0; t < teams.size(); ++t)
+    for (int j : members[t]) tp.team_of[j] = (int)t;
+  tp.teams = teams;
+  tp.nblocks = nblocks;
+  return tp;
+}
+
+// One launch: PCG solves (apply = 0) or single K*v products (apply = 1) of the
+// listed problems.  Teams: problems whose share of the total cost is worth
+// two or more CTAs get their own team of that size; the rest are packed onto
+// single-CTA teams, largest first onto the least-loaded team.
+kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
+                           const std::vector<int> &idx, const std::vector<const double *> &rhs,
+                           const std::vector<double *> &out, const std::vector<double> &tol,
+                           const std::vector<int> &maxit, int apply, int prec, cudaStream_t s,
+                           std::vector<int> &iters, std::vector<int> &errs,
+                           std::vector<double> &rr, std::vector<double> &bb, float *ms,
+                           std::string &err, const std::vector<double> *weight) {
+  const int k = (int)idx.size();
+  iters.assign(k, 0); errs.assign(k, 0); rr.assign(k, 0.0); bb.assign(k, 0.0);
+  if (k == 0) { if (ms) *ms = 0.f; return KQ_OK; }
+  const TeamPlan tp = plan_teams(B.G, hs, idx, weight, &B.tune);
+  const std::vector<TeamInfo> &teams = tp.teams;
+  const int nblocks = tp.nblocks;
+  const std::vector<int> &cta_team = tp.cta_team, &team_qps = tp.team_qps;
   // ---- per-problem arguments
   std::vector<PcgArgs> args(k);
-  std::vector<int> team_of(k, 0);
-  for (size_t t = 0; t < teams.size(); ++t)
-    for (int j : members[t]) team_of[j] = (int)t;
+  const std::vector<int> &team_of = tp.team_of;
   size_t smem = 0;
   for (int j = 0; j < k; ++j) {
     kq_problem *h = hs[idx[j]];
@@ -2011,6 +2078,8 @@ kq_status batch_pcg_launch(BatchPcg &B, const std::vector<kq_problem *> &hs,
     a.stag_window = (prec == KQ_PREC_MIXED && !apply) ? W.stag_window : 0;
     a.coefA = W.coefA;
     a.dinv = W.dinv;
+    a.run = 1;
+    a.colpass_min_n = B.tune.colpass_min_n;
     smem = std::max(smem, (size_t)2 * a.win_cap * (prec == KQ_PREC_MIXED ? sizeof(float) : sizeof(double)));
     if (cudaMemsetAsync(W.bar, 0, 2 * sizeof(unsigned int), s) != cudaSuccess) { err = "memset"; return KQ_ERR_CUDA; }
   }
@@ -2672,4 +2741,323 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
   s.status = rc;
   if (st) *st = s;
   return rc;
+}
+
+// ---------------------------------------------------------------- batched solver, captured graph
+// The lock-step IPM iteration of the batch is captured once in a CUDA graph
+// (batch.cu) and replayed; every decision the host made between launches is
+// taken on the device from per-QP control words (QpCtl): which precision a
+// correction pass runs in, when a Newton solve stops, the step lengths, the
+// mu rule and when a QP is done.  Three argument arrays live on the device
+// (FP32 solve, FP64 solve, FP64 apply), built before capture; the control
+// kernels only switch problems on and off and set their tolerances.
+namespace {
+
+__device__ __forceinline__ PcgArgs *gargs_of(unsigned char *g, int which, int nq) {
+  return reinterpret_cast<PcgArgs *>(g) + (size_t)which * nq;
+}
+
+__global__ void k_gctl_pcg_init(QpCtl *ctl, int nq, int mixed) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    QpCtl &c = ctl[q];
+    c.pcg_done = c.active ? 0 : 1;
+    c.used = 0;
+    c.fp32_ok = mixed;
+    c.resn = 0.0;
+    c.bnorm = 0.0;
+    c.ran = 0;
+  }
+}
+
+// pass setup: precision and relative tolerance of this correction pass
+__global__ void k_gctl_pass_setup(QpCtl *ctl, unsigned char *g, int nq, int pass, double tol,
+                                  double inner_tol, int maxit, int refine_steps) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    QpCtl &c = ctl[q];
+    PcgArgs *a32 = gargs_of(g, 0, nq) + q, *a64 = gargs_of(g, 1, nq) + q, *aap = gargs_of(g, 2, nq) + q;
+    int run = c.active && !c.pcg_done;
+    if (run && maxit - c.used <= 0) { c.pcg_done = 1; run = 0; }
+    const int prec = (c.fp32_ok && pass < refine_steps) ? KQ_PREC_MIXED : KQ_PREC_F64;
+    double rel = pass == 0 ? tol : tol * c.bnorm / fmax(c.resn, 1e-300);
+    if (prec == KQ_PREC_MIXED) rel = fmax(rel, inner_tol);
+    rel = fmin(rel, 0.5);
+    PcgArgs *as = prec == KQ_PREC_MIXED ? a32 : a64;
+    as->tol2 = rel * rel;
+    as->maxit = maxit - c.used;
+    a32->run = run && prec == KQ_PREC_MIXED;
+    a64->run = run && prec == KQ_PREC_F64;
+    aap->run = run;
+    c.ran = run;
+    c.prec = prec;
+    c.resn_before = c.resn;
+    c.tol_rel = tol;
+  }
+}
+
+// pass finish: iterations, the true residual |rhs - K z| (reduced by the
+// handle's kernels into redout[q][8]), the FP32 rule, stop or continue
+__global__ void k_gctl_pass_finish(QpCtl *ctl, const int *iters, const int *errs, const double *resn,
+                                   double *const *redout, int nq, int pass, int last, int maxit) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    QpCtl &c = ctl[q];
+    if (!c.ran) continue;
+    const int reg = c.prec == KQ_PREC_MIXED ? 0 : 1;
+    const int e = errs[reg * nq + q] ? errs[reg * nq + q] : errs[2 * nq + q];
+    if (e) {
+      c.status = e == 7 ? KQ_ERR_TIMEOUT : (e == 4 ? KQ_ERR_NOT_CONVEX : KQ_ERR_NUMERIC);
+      c.active = 0;
+      c.pcg_done = 1;
+      continue;
+    }
+    const int its = iters[reg * nq + q];
+    if (pass == 0) c.bnorm = sqrt(resn[2 * (reg * nq + q) + 1]);
+    c.used += its;
+    c.pcg_iters += its;
+    const double rn = sqrt(redout[q][8]);
+    if (!(rn == rn)) {
+      c.status = KQ_ERR_NUMERIC;
+      c.active = 0;
+      c.pcg_done = 1;
+      continue;
+    }
+    c.resn = rn;
+    if (c.prec == KQ_PREC_MIXED && pass > 0 && rn > 0.5 * c.resn_before) c.fp32_ok = 0;
+    if (c.prec == KQ_PREC_MIXED && pass == 0 && rn > 0.5 * c.bnorm) c.fp32_ok = 0;
+    if (rn <= c.tol_rel * c.bnorm || c.bnorm == 0.0) {
+      c.pcg_done = 1;
+    } else if (c.used >= maxit) {
+      c.pcg_done = 1;
+      c.maxit_hits++;
+    } else if (last) {
+      c.maxit_hits++;   // passes used up with the tolerance not met; the step is taken
+    }
+  }
+}
+
+// step lengths of Eq. (10) from the ratio-test minima (redout[q][4..5])
+__global__ void k_gctl_step(QpCtl *ctl, double *const *redout, int nq, double gamma) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    QpCtl &c = ctl[q];
+    if (!c.active) continue;
+    c.ax = fmin(1.0, gamma * redout[q][4]);
+    c.al = fmin(1.0, gamma * redout[q][5]);
+    if (!(c.ax == c.ax) || !(c.al == c.al)) {
+      c.status = KQ_ERR_NUMERIC;
+      c.active = 0;
+    }
+  }
+}
+
+// the mu rule of Algorithm 1 from |r|^2 (redout[q][10..14]): return when
+// |r| < mu and mu < mu_tol, else divide mu by 10 when |r| < mu
+__global__ void k_gctl_mu_rule(QpCtl *ctl, double *const *redout, int nq, double mu0, double mu_tol) {
+  for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
+    QpCtl &c = ctl[q];
+    if (!c.active) continue;
+    const double *r = redout[q] + 10;
+    const double rn = sqrt(r[0] + r[1] + r[2] + r[3] + r[4]);
+    c.ipm_iters++;
+    if (!(rn == rn)) {
+      c.status = KQ_ERR_NUMERIC;
+      c.active = 0;
+      continue;
+    }
+    if (rn < c.mu) {
+      if (c.mu < mu_tol) {
+        c.active = 0;
+        c.status = KQ_OK;
+      } else {
+        c.kexp++;
+        c.mu = mu0 * pow(10.0, -(double)c.kexp);
+      }
+    }
+  }
+}
+
+__global__ void k_gctl_count(const QpCtl *ctl, int nq, int *count) {
+  __shared__ int s;
+  if (threadIdx.x == 0) s = 0;
+  __syncthreads();
+  int c = 0;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) c += ctl[q].active;
+  atomicAdd(&s, c);
+  __syncthreads();
+  if (threadIdx.x == 0) *count = s;
+}
+
+// which: 0 = the correction pass (each problem in its own precision), 2 = FP64 apply
+template <class HS, class AS>
+const void *batch_kernel_of(int which) {
+  return which == 0 ? (const void *)pcg_batch_kernel_dual<HS, AS>
+                    : (const void *)pcg_batch_kernel<HS, AS, double>;
+}
+
+const void *graph_kernel(const kq_problem *h0, int which) {
+  if (h0->P.hdtype == KQ_BF16 && h0->P.adtype == KQ_F32) return batch_kernel_of<__nv_bfloat16, float>(which);
+  if (h0->P.hdtype == KQ_F64 && h0->P.adtype == KQ_F64) return batch_kernel_of<double, double>(which);
+  return nullptr;
+}
+
+}  // namespace
+
+kq_status batch_graph_prepare(BatchPcg &B, const std::vector<kq_problem *> &hs,
+                              const std::vector<double> &weight, std::string &err) {
+  const int nq = (int)hs.size();
+  if (!B.gargs) {
+    B.gargs = balloc<unsigned char>(B.allocs, 3 * (size_t)nq * sizeof(PcgArgs));
+    B.ctl = balloc<QpCtl>(B.allocs, nq);
+    B.redout = balloc<double *>(B.allocs, nq);
+    B.g_iters = balloc<int>(B.allocs, 3 * (size_t)nq);
+    B.g_err = balloc<int>(B.allocs, 3 * (size_t)nq);
+    B.g_resn = balloc<double>(B.allocs, 6 * (size_t)nq);
+    B.d_count = balloc<int>(B.allocs, 1);
+    if (!B.gargs || !B.ctl || !B.redout || !B.g_iters || !B.g_err || !B.g_resn || !B.d_count) {
+      err = "batch graph work space";
+      return KQ_ERR_OOM;
+    }
+    if (cudaMallocHost((void **)&B.h_count, sizeof(int)) != cudaSuccess) {
+      err = "batch graph pinned count";
+      return KQ_ERR_OOM;
+    }
+    std::vector<double *> ro(nq);
+    for (int q = 0; q < nq; ++q) ro[q] = hs[q]->red_out;
+    if (cudaMemcpy(B.redout, ro.data(), nq * sizeof(double *), cudaMemcpyHostToDevice) != cudaSuccess) {
+      err = "batch graph pointers";
+      return KQ_ERR_CUDA;
+    }
+  }
+  // teams over the problems still iterating (weight > 0)
+  std::vector<int> idx;
+  std::vector<double> w;
+  for (int q = 0; q < nq; ++q)
+    if (weight[q] > 0.0) { idx.push_back(q); w.push_back(weight[q]); }
+  TeamPlan tp;
+  if (!idx.empty()) tp = plan_teams(B.G, hs, idx, &w, &B.tune);
+  std::vector<int> team_size(nq, 1);
+  for (size_t j = 0; j < idx.size(); ++j) team_size[idx[j]] = tp.teams[tp.team_of[j]].size;
+  for (int &j : tp.team_qps) j = idx[j];          // list positions -> problem indices
+  std::vector<PcgArgs> args(3 * (size_t)nq);
+  size_t smem[3] = {0, 0, 0};
+  for (int which = 0; which < 3; ++which) {
+    for (int q = 0; q < nq; ++q) {
+      kq_problem *h = hs[q];
+      PcgWork &W = h->W;
+      PcgArgs &a = args[(size_t)which * nq + q];
+      a = PcgArgs{};
+      a.P = h->P;
+      a.Dl = h->K.Dl; a.Du = h->K.Du; a.cl = h->K.cl; a.cu = h->K.cu;
+      a.dg = h->K.dg; a.diag = h->K.diag; a.mu = h->K.mu;
+      a.apply = which == 2;
+      a.rhs = a.apply ? h->z : h->tmp;
+      a.z = h->zref;
+      a.r = W.r; a.y = W.y; a.pb0 = W.pb0; a.pb1 = W.pb1; a.qlam = W.qlam;
+      a.accx = which == 0 ? (void *)W.accx32 : (void *)W.accx64;
+      a.g = nullptr; a.slots = W.slots;
+      a.win_cap = (int)((h->n + 7) & ~(int64_t)7);
+      a.bar.count = W.bar; a.bar.gen = W.bar + 1; a.bar.err = B.g_err + (size_t)which * nq + q;
+      a.bar.nblocks = (unsigned)team_size[q];
+      a.bar.budget_ns = (uint64_t)(h->timeout_s * 1e9);
+      a.tol2 = 0.0; a.maxit = 0;
+      a.iters = B.g_iters + (size_t)which * nq + q;
+      a.resn = B.g_resn + 2 * ((size_t)which * nq + q);
+      a.stages = 2; a.producer = 0; a.copy_piece = 16;
+      a.stag_window = which == 0 ? W.stag_window : 0;
+      a.coefA = W.coefA;
+      a.dinv = W.dinv;
+      a.run = 0;
+      a.colpass_min_n = B.tune.colpass_min_n;
+      if (weight[q] > 0.0)
+        smem[which] = std::max(smem[which], (size_t)2 * a.win_cap * (which == 0 ? sizeof(float) : sizeof(double)));
+    }
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpy(B.gargs, args.data(), args.size() * sizeof(PcgArgs), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemset(B.g_err, 0, 3 * (size_t)nq * sizeof(int))) != cudaSuccess) {
+    err = std::string("batch graph arguments: ") + cudaGetErrorString(e);
+    return KQ_ERR_CUDA;
+  }
+  // grid-barrier counters start at zero; within one capture every launch of
+  // a problem uses the same team size, so the counter stays a multiple of it
+  for (int q = 0; q < nq; ++q)
+    if (cudaMemset(hs[q]->W.bar, 0, 2 * sizeof(unsigned int)) != cudaSuccess) {
+      err = "batch graph barrier reset";
+      return KQ_ERR_CUDA;
+    }
+  B.gblocks = tp.nblocks;
+  if (B.gblocks > 0) {
+    if ((e = cudaMemcpy(B.cta_team, tp.cta_team.data(), tp.nblocks * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(B.teams, tp.teams.data(), tp.teams.size() * sizeof(TeamInfo), cudaMemcpyHostToDevice)) != cudaSuccess ||
+        (e = cudaMemcpy(B.team_qps, tp.team_qps.data(), tp.team_qps.size() * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess) {
+      err = std::string("batch graph teams: ") + cudaGetErrorString(e);
+      return KQ_ERR_CUDA;
+    }
+    smem[0] = std::max(smem[0], smem[1]);   // the pass launch runs either precision
+    for (int which : {0, 2}) {
+      const void *f = graph_kernel(hs[0], which);
+      if (!f) { err = "batched PCG supports bf16 H with f32 A, or f64 H with f64 A"; return KQ_ERR_ARG; }
+      B.gsmem[which] = std::max<size_t>(smem[which], 16);
+      int per_sm = 0;
+      if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)B.gsmem[which]) != cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, f, 512, B.gsmem[which]) != cudaSuccess ||
+          per_sm * B.G < B.gblocks) {
+        err = "batched PCG grid does not fit";
+        return KQ_ERR_ARG;
+      }
+    }
+  }
+  return KQ_OK;
+}
+
+// one batched launch of kind `which` (0: the correction pass, each problem in
+// its own precision; 2: FP64 apply) as a cooperative launch that stream
+// capture records as a graph node
+kq_status batch_graph_launch(BatchPcg &B, const kq_problem *h0, int which, cudaStream_t s,
+                             std::string &err) {
+  if (B.gblocks == 0) return KQ_OK;
+  const void *f = graph_kernel(h0, which);
+  PcgArgs *pa = reinterpret_cast<PcgArgs *>(B.gargs) + (size_t)which * B.nqp;
+  PcgArgs *p64 = reinterpret_cast<PcgArgs *>(B.gargs) + (size_t)B.nqp;
+  const TeamInfo *pt = reinterpret_cast<const TeamInfo *>(B.teams);
+  void *kargs_pass[] = {(void *)&pa, (void *)&p64, (void *)&B.cta_team, (void *)&pt, (void *)&B.team_qps};
+  void *kargs_one[] = {(void *)&pa, (void *)&B.cta_team, (void *)&pt, (void *)&B.team_qps};
+  void **kargs = which == 0 ? kargs_pass : kargs_one;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(B.gblocks);
+  cfg.blockDim = dim3(512);
+  cfg.dynamicSmemBytes = B.gsmem[which];
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const cudaError_t e = cudaLaunchKernelExC(&cfg, f, kargs);
+  if (e != cudaSuccess) {
+    err = std::string("batch graph launch: ") + cudaGetErrorString(e);
+    return KQ_ERR_CUDA;
+  }
+  B.launches++;
+  return KQ_OK;
+}
+
+void batch_graph_pcg_init(BatchPcg &B, int mixed, cudaStream_t s) {
+  k_gctl_pcg_init<<<(B.nqp + 255) / 256, 256, 0, s>>>(B.ctl, B.nqp, mixed);
+}
+void batch_graph_pass_setup(BatchPcg &B, int pass, const kq_pcg_opts &o, cudaStream_t s) {
+  k_gctl_pass_setup<<<(B.nqp + 255) / 256, 256, 0, s>>>(B.ctl, B.gargs, B.nqp, pass, o.tol, o.inner_tol,
+                                                        o.maxit, o.precision == KQ_PREC_MIXED ? o.refine_steps : 0);
+}
+void batch_graph_pass_finish(BatchPcg &B, int pass, int last, int maxit, cudaStream_t s) {
+  k_gctl_pass_finish<<<(B.nqp + 255) / 256, 256, 0, s>>>(B.ctl, B.g_iters, B.g_err, B.g_resn, B.redout,
+                                                         B.nqp, pass, last, maxit);
+}
+void batch_graph_step(BatchPcg &B, double gamma, cudaStream_t s) {
+  k_gctl_step<<<(B.nqp + 255) / 256, 256, 0, s>>>(B.ctl, B.redout, B.nqp, gamma);
+}
+void batch_graph_mu_rule(BatchPcg &B, double mu0, double mu_tol, cudaStream_t s) {
+  k_gctl_mu_rule<<<(B.nqp + 255) / 256, 256, 0, s>>>(B.ctl, B.redout, B.nqp, mu0, mu_tol);
+}
+void batch_graph_count(BatchPcg &B, cudaStream_t s) {
+  k_gctl_count<<<1, 256, 0, s>>>(B.ctl, B.nqp, B.d_count);
+  cudaMemcpyAsync(B.h_count, B.d_count, sizeof(int), cudaMemcpyDeviceToHost, s);
 }

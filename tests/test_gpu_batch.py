@@ -120,3 +120,32 @@ def test_c3_largest_against_oracle(kq, prec):
         dx = np.max(np.abs(out["x"][g["x_idx"]] - np.array(g["x_at_idx"]))) / (1 + g["x_inf"])
         print("  x distance at sampled indices %.2e" % dx)
     kq.qp_batch_destroy(b)
+
+
+@pytest.mark.parametrize("prec", [1, 0], ids=["mixed", "f64"])
+def test_graph_replay_matches_host_driven(kq, prec):
+    """The lock-step IPM iteration captured once in a CUDA graph and
+    replayed, every decision (pass precision, PCG stop, step lengths, mu
+    rule, done) taken on the device, gives the host-driven solver's solution
+    and the oracle's; the graph is captured again only when QPs finish."""
+    sizes = qpgen.batch_sizes(24, 16, 600, size_seed=11)
+    qps = [qpgen.batch_qp(k, n) for k, n in enumerate(sizes)]
+    res = {}
+    for graph in (1, 0):
+        b = kq.qp_create_batch(qps)
+        xs = [np.zeros(q.n) for q in qps]
+        rc, status, st = kq.ipm_solve_batch(b, kq.default_ipm_opts(precision=prec, graph=graph), xs)
+        print("graph", graph, st.as_dict())
+        assert rc == kq.KQ_OK and all(s_ == kq.KQ_OK for s_ in status)
+        if graph:
+            assert 1 <= st.graph_captures <= len(qps) and st.graph_replays == st.ipm_iters_max
+            for k in (0, len(qps) // 2, len(qps) - 1):
+                _check_against_oracle(kq, b, k, qps[k], xs[k], ("graph", k))
+        res[graph] = (xs, st)
+        kq.qp_batch_destroy(b)
+    for k, q in enumerate(qps):
+        f1, f0 = q.objective(res[1][0][k]), q.objective(res[0][0][k])
+        assert abs(f1 - f0) <= 1e-6 * (1 + abs(f0)), (k, f1, f0)
+    # the same Algorithm 1 (the atomics' summation order may move a
+    # borderline mu test by one iteration on a few QPs)
+    assert abs(res[1][1].ipm_iters_total - res[0][1].ipm_iters_total) <= len(qps)

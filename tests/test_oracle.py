@@ -518,3 +518,18 @@ def test_weighted_lowrank_unconstrained_closed_form():
     xstar = -np.linalg.solve(H, qp.p)
     assert res.status == "converged"
     assert np.max(np.abs(res.x - xstar)) <= 1e-10 * (1 + np.max(np.abs(xstar)))
+
+
+def test_infeasibilities_split_the_residual_norm():
+    """Section 5.2's primal, dual and complementarity infeasibilities cover
+    the ten blocks of Eq. (7) between them: on the hand-worked example,
+    primal^2 = r_e^2 + r_lA^2 + r_uA^2 + r_lx^2 + r_ux^2 = 0.0025 + 0.36 +
+    0.16 + 1.25 + 0.0625, dual^2 = |r_H|^2 = 15.725, compl^2 = 8.41 + 0.16 +
+    0.32 + 0.81."""
+    S = I.scale(_worked_qp())
+    r = I.residuals(S, _worked_state(), 0.1)
+    pr, du, co = I.infeasibilities(r)
+    assert pr ** 2 == pytest.approx(1.835, rel=1e-13)
+    assert du ** 2 == pytest.approx(15.725, rel=1e-13)
+    assert co ** 2 == pytest.approx(9.7, rel=1e-13)
+    assert pr ** 2 + du ** 2 + co ** 2 == pytest.approx(WORKED_NORM2, rel=1e-13)
