@@ -107,10 +107,10 @@ typedef struct {
   int ipm_maxit;           /* Algorithm 1's N (200)                             */
   double pcg_tol;          /* relative unpreconditioned residual (1e-7)         */
   int pcg_maxit;           /* PCG iterations per Newton solve (5000)            */
-  int precision;           /* KQ_PREC_*.  MIXED: once a Newton solve needs FP64  */
-                           /* correction iterations and an FP64 product costs   */
-                           /* under twice an FP32 iteration (latency-bound      */
-                           /* problems), the rest of the solve runs in FP64     */
+  int precision;           /* KQ_PREC_*.  MIXED: once a Newton solve has timed  */
+                           /* an FP64 product (its residual check) at under     */
+                           /* twice an FP32 iteration (latency-bound problems), */
+                           /* the rest of the solve runs in FP64                */
   int refine_steps;        /* MIXED: FP32 correction solves before FP64 (6); the */
                            /* batched solver hands a QP to FP64 earlier once one*/
                            /* of its FP32 solves fails to halve its residual    */

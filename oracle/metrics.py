@@ -118,7 +118,7 @@ def kkt_metrics(qp, x, lam_lA, lam_uA, lam_lx, lam_ux, lam_e):
     if me:
         gap += float(np.asarray(lam_e, float) @ (C @ x - qp.b))
     return {"primal_rel": primal, "dual_rel": dual, "compl_rel": compl,
-            "kkt_rel": max(primal, dual), "objective": f, "gap": gap,
+            "kkt_rel": max(primal, dual), "dual_scale": scale, "objective": f, "gap": gap,
             "gap_rel": abs(gap) / (1.0 + abs(f))}
 
 

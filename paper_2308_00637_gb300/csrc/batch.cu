@@ -174,6 +174,7 @@ kq_status enqueue_iteration(kq_batch b, const kq_ipm_opts &o, const kq_pcg_opts 
   }
   for (int pass = 0; pass < max_passes; ++pass) {
     batch_graph_pass_setup(B, pass, po, s);
+    batch_graph_schedule(B, s);   // teams over the QPs that run in this pass
     kq_status rc;
     if ((rc = batch_graph_launch(B, hs[0], 0, s, e)) != KQ_OK) return bfail(b, rc, e);
     for (int q : act) vec_add_enqueue(hs[q], hs[q]->z, hs[q]->zref);

@@ -1403,10 +1403,11 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
   kq_status final = KQ_ERR_IPM_MAXIT;
   const DevProb &P = h->P;
   int it = 0;
-  // Mixed precision pays where a product is bandwidth-bound.  Once a Newton
-  // solve needed FP64 correction iterations (its FP32 passes stalled) and an
-  // FP64 product costs less than twice an FP32 iteration (a latency-bound
-  // problem), the rest of the solve runs in FP64 (KQ_MIXED_SWITCH=0: never).
+  // Mixed precision pays where a product is bandwidth-bound.  Every mixed
+  // Newton solve times its FP64 residual products; when an FP64 product costs
+  // less than twice an FP32 iteration (a latency-bound problem, where FP32
+  // passes only add iterations), the rest of the solve runs in FP64
+  // (KQ_MIXED_SWITCH=0: never).
   bool to_f64 = false;
   const char *msw = getenv("KQ_MIXED_SWITCH");
   const bool allow_switch = !(msw && atoi(msw) == 0);
@@ -1436,7 +1437,8 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
       rec.lanczos_max = h->lz_max;
       rec.kappa_jacobi = h->lz_min > 0.0 ? h->lz_max / h->lz_min : 0.0;
     }
-    if (o.precision == KQ_PREC_MIXED && !to_f64 && allow_switch && ps.iters_f64 > 0) {
+    if (o.precision == KQ_PREC_MIXED && !to_f64 && allow_switch && ps.products_f64 > 0 &&
+        ps.iters > ps.iters_f64) {
       const double t32 = (ps.kernel_ms - ps.kernel_ms_f64) / std::max(1, ps.iters - ps.iters_f64);
       const double t64 = ps.kernel_ms_f64 / std::max(1, ps.products_f64);
       if (t64 < 2.0 * t32) {

@@ -63,6 +63,7 @@ struct QpCtl {
   int pcg_done;      // the current Newton solve has finished
   int fp32_ok;       // FP32 correction passes still pay for this QP
   int used;          // PCG iterations of the current Newton solve
+  int w_prev;        // PCG iterations of the previous Newton solve (team costs)
   int kexp;          // mu = mu0 10^-kexp
   int ipm_iters;
   int status;        // KQ_OK once converged; an error code if a step failed
@@ -299,6 +300,11 @@ struct BatchPcg {
   int *d_count = nullptr, *h_count = nullptr;
   int gblocks = 0;
   size_t gsmem[3] = {0, 0, 0};
+  // device-side team plan before every correction pass (dev_sched): the
+  // per-product cost and the team-size cap of every QP
+  int dev_sched = 0;
+  double *q_cost = nullptr;
+  int *q_cap = nullptr;
   std::vector<void *> allocs;
   unsigned char *args = nullptr, *teams = nullptr;
   int *cta_team = nullptr, *team_qps = nullptr;
@@ -327,6 +333,7 @@ kq_status batch_graph_launch(BatchPcg &B, const kq_problem *h0, int which, cudaS
                              std::string &err);
 void batch_graph_pcg_init(BatchPcg &B, int mixed, cudaStream_t s);
 void batch_graph_pass_setup(BatchPcg &B, int pass, const kq_pcg_opts &o, cudaStream_t s);
+void batch_graph_schedule(BatchPcg &B, cudaStream_t s);
 void batch_graph_pass_finish(BatchPcg &B, int pass, int last, int maxit, cudaStream_t s);
 void batch_graph_step(BatchPcg &B, double gamma, cudaStream_t s);
 void batch_graph_mu_rule(BatchPcg &B, double mu0, double mu_tol, cudaStream_t s);

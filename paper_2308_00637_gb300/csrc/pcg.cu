@@ -1634,7 +1634,9 @@ __global__ void __launch_bounds__(512, 1) pcg_batch_kernel(const PcgArgs *__rest
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sh[32 * 2];
   __shared__ double sbuf[512];
-  const TeamInfo ti = teams[cta_team[blockIdx.x]];
+  const int tix = cta_team[blockIdx.x];
+  if (tix < 0) return;              // a CTA the device-side plan left idle
+  const TeamInfo ti = teams[tix];
   const int rank = blockIdx.x - ti.first_cta;
   for (int q = ti.qp_begin; q < ti.qp_end; ++q) {
     const PcgArgs &aq = args[team_qps[q]];
@@ -1656,7 +1658,9 @@ __global__ void __launch_bounds__(512, 1) pcg_batch_kernel_dual(const PcgArgs *_
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ double sh[32 * 2];
   __shared__ double sbuf[512];
-  const TeamInfo ti = teams[cta_team[blockIdx.x]];
+  const int tix = cta_team[blockIdx.x];
+  if (tix < 0) return;              // a CTA the device-side plan left idle
+  const TeamInfo ti = teams[tix];
   const int rank = blockIdx.x - ti.first_cta;
   for (int q = ti.qp_begin; q < ti.qp_end; ++q) {
     const int j = team_qps[q];
@@ -1958,23 +1962,34 @@ int size_bucket(int64_t n, int nb) {
   return b;
 }
 
+// cost of one K*v product of a batched problem: the autotuner's measured
+// one-CTA time of its size bucket, else its bytes
+double unit_cost(const kq_problem *h, const BatchTune *tune) {
+  if (tune && !tune->t_prod_us.empty())
+    return tune->t_prod_us[size_bucket(h->n, (int)tune->t_prod_us.size())];
+  const double hb = h->P.hdtype == KQ_F64 ? 8.0 : (h->P.hdtype == KQ_F32 ? 4.0 : 2.0);
+  const double ab = h->P.adtype == KQ_F64 ? 8.0 : 4.0;
+  return hb * h->n * h->n + ab * h->m * h->n + 64.0 * h->nkp;
+}
+
+// largest team of a batched problem: two rows of H, A, C per warp of the
+// team, the CTAs its slot buffer holds, and the tuned cap of its size bucket
+int team_cap(const kq_problem *h, const BatchTune *tune) {
+  int t = (int)std::min<int64_t>(ceil_div64(h->n + h->m + h->me, 32), h->num_sms);
+  if (tune && !tune->team_cap.empty())
+    t = std::min(t, tune->team_cap[size_bucket(h->n, (int)tune->team_cap.size())]);
+  return std::max(t, 1);
+}
+
 TeamPlan plan_teams(int G, const std::vector<kq_problem *> &hs, const std::vector<int> &idx,
                     const std::vector<double> *weight, const BatchTune *tune = nullptr) {
   const int k = (int)idx.size();
   TeamPlan tp;
-  const bool tuned = tune && !tune->t_prod_us.empty();
-  const int nb = tuned ? (int)tune->t_prod_us.size() : 0;
-  // ---- costs: bytes per product times the expected number of products
+  // ---- costs: cost per product times the expected number of products
   std::vector<double> cost(k);
   double total = 0.0;
   for (int j = 0; j < k; ++j) {
-    const kq_problem *h = hs[idx[j]];
-    const double hb = h->P.hdtype == KQ_F64 ? 8.0 : (h->P.hdtype == KQ_F32 ? 4.0 : 2.0);
-    const double ab = h->P.adtype == KQ_F64 ? 8.0 : 4.0;
-    // measured time of one product (autotuner) or its bytes
-    const double per = tuned ? tune->t_prod_us[size_bucket(h->n, nb)]
-                             : hb * h->n * h->n + ab * h->m * h->n + 64.0 * h->nkp;
-    cost[j] = per * (weight ? std::max(1.0, (*weight)[j]) : 1.0);
+    cost[j] = unit_cost(hs[idx[j]], tune) * (weight ? std::max(1.0, (*weight)[j]) : 1.0);
     total += cost[j];
   }
   std::vector<int> order(k);
@@ -1987,11 +2002,8 @@ TeamPlan plan_teams(int G, const std::vector<kq_problem *> &hs, const std::vecto
   for (; q < order.size(); ++q) {
     const int j = order[q];
     int t = (int)std::floor(G * cost[j] / total);
-    // at most two rows of H, A, C per warp of the team
     const kq_problem *hj = hs[idx[j]];
-    t = (int)std::min<int64_t>(t, ceil_div64(hj->n + hj->m + hj->me, 32));
-    t = std::min(t, hj->num_sms);     // the problem's slot buffer holds up to num_sms CTAs
-    if (tuned) t = std::min(t, tune->team_cap[size_bucket(hj->n, nb)]);
+    t = std::min(t, team_cap(hj, tune));
     if (tune && tune->force_team > 0 && k == 1) t = std::min(tune->force_team, hj->num_sms);
     // keep one CTA for the problems packed onto single CTAs, unless none is
     // left to pack; a team that does not fit is shrunk, not dropped (a
@@ -2761,6 +2773,7 @@ __global__ void k_gctl_pcg_init(QpCtl *ctl, int nq, int mixed) {
   for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nq; q += gridDim.x * blockDim.x) {
     QpCtl &c = ctl[q];
     c.pcg_done = c.active ? 0 : 1;
+    if (c.used > 0) c.w_prev = c.used;
     c.used = 0;
     c.fp32_ok = mixed;
     c.resn = 0.0;
@@ -2885,6 +2898,135 @@ __global__ void k_gctl_count(const QpCtl *ctl, int nq, int *count) {
   if (threadIdx.x == 0) *count = s;
 }
 
+// The team plan of one correction pass made on the device (the captured
+// graph's counterpart of plan_teams, same rule): over the QPs that run in
+// this pass (ctl.ran), costed by their cost per product times the iterations
+// of their previous Newton solve, a QP worth two or more CTAs gets a team of
+// that size (capped, shrunk to the room left); the rest are packed onto
+// single-CTA teams, costliest first onto the least-loaded one.  One CTA of
+// 1024 threads.  Writes cta_team (-1: idle CTA), teams, team_qps, the team
+// size of every running QP into its three argument records, and zeroes the
+// grid-barrier counters of the running QPs (team sizes change between passes;
+// the barrier needs a counter that is a multiple of the team size).
+constexpr int KQ_SCHED_MAX_Q = 2048;
+
+size_t schedule_smem(int nq, int G) {
+  return (size_t)(nq + G) * sizeof(double) + (size_t)(2 * nq + G + 1) * sizeof(int);
+}
+
+__global__ void __launch_bounds__(1024) k_gctl_schedule(const QpCtl *__restrict__ ctl, unsigned char *g,
+                                                       int nq, int G, const double *__restrict__ q_cost,
+                                                       const int *__restrict__ q_cap, int *cta_team,
+                                                       TeamInfo *teams, int *team_qps) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double *cost = reinterpret_cast<double *>(sm);     // nq: cost of a running QP, -1 otherwise
+  double *load = cost + nq;                          // G: load of each single-CTA team
+  int *order = reinterpret_cast<int *>(load + G);    // k: running QPs, costliest first
+  int *bin = order + nq;                             // single-CTA team of order[i]
+  int *off = bin + nq;                               // G + 1: member offsets of those teams
+  __shared__ double s_red[64];
+  __shared__ double s_total;
+  __shared__ int s_k, s_qpos, s_used, s_nsingle;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  double v[2] = {0.0, 0.0};   // total cost, running QPs
+  for (int q = tid; q < nq; q += nt) {
+    const QpCtl &c = ctl[q];
+    const double w = c.ran ? q_cost[q] * (double)max(1, c.w_prev) : -1.0;
+    cost[q] = w;
+    if (c.ran) { v[0] += w; v[1] += 1.0; }
+  }
+  block_sum<2>(v, s_red);
+  if (tid == 0) { s_total = v[0]; s_k = (int)(v[1] + 0.5); }
+  __syncthreads();
+  const double total = s_total;
+  const int k = s_k;
+  // rank of every running QP: costlier first, ties to the lower index
+  for (int q = tid; q < nq; q += nt) {
+    const double cq = cost[q];
+    if (cq < 0.0) continue;
+    int r = 0;
+    for (int p = 0; p < nq; ++p) {
+      const double cp = cost[p];
+      r += (cp > cq) || (cp == cq && p < q);
+    }
+    order[r] = q;
+  }
+  __syncthreads();
+  // teams of two or more CTAs (sequential: each takes from the room left)
+  if (tid == 0) {
+    int used = 0, i = 0;
+    for (; i < k; ++i) {
+      const int j = order[i];
+      int t = (int)floor((double)G * cost[j] / total);
+      t = min(t, q_cap[j]);
+      const int room = (i + 1 < k) ? G - 1 - used : G - used;
+      t = min(t, room);
+      if (t < 2) break;
+      teams[i] = TeamInfo{used, t, i, i + 1};
+      team_qps[i] = j;
+      used += t;
+    }
+    s_qpos = i;
+    s_used = used;
+    s_nsingle = (i < k) ? max(1, G - used) : 0;
+  }
+  __syncthreads();
+  const int qpos = s_qpos, used = s_used, nsingle = s_nsingle;
+  for (int c = tid; c < nsingle; c += nt) load[c] = 0.0;
+  __syncthreads();
+  // the rest onto single-CTA teams: costliest first onto the least-loaded
+  // team (ties to the lower team), one warp
+  if (tid < 32) {
+    for (int i = qpos; i < k; ++i) {
+      double best = INFINITY;
+      int bi = 0x7fffffff;
+      for (int c = lane; c < nsingle; c += 32) {
+        const double l = load[c];
+        if (l < best) { best = l; bi = c; }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob < best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+      }
+      if (lane == 0) {
+        load[bi] += cost[order[i]];
+        bin[i] = bi;
+      }
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int c = 0; c <= nsingle; ++c) off[c] = 0;
+    for (int i = qpos; i < k; ++i) off[bin[i] + 1]++;
+    for (int c = 0; c < nsingle; ++c) off[c + 1] += off[c];
+    for (int c = 0; c < nsingle; ++c)
+      teams[qpos + c] = TeamInfo{used + c, 1, qpos + off[c], qpos + off[c + 1]};
+    for (int i = qpos; i < k; ++i) team_qps[qpos + off[bin[i]]++] = order[i];
+  }
+  __syncthreads();
+  for (int x = tid; x < G; x += nt) {
+    int t = -1;
+    if (x >= used) {
+      if (x < used + nsingle) t = qpos + (x - used);
+    } else {
+      for (int i = 0; i < qpos; ++i)
+        if (x >= teams[i].first_cta && x < teams[i].first_cta + teams[i].size) { t = i; break; }
+    }
+    cta_team[x] = t;
+  }
+  for (int i = tid; i < k; i += nt) {
+    const int j = order[i];
+    const unsigned size = i < qpos ? (unsigned)teams[i].size : 1u;
+    for (int w = 0; w < 3; ++w) gargs_of(g, w, nq)[j].bar.nblocks = size;
+    const PcgArgs &a = gargs_of(g, 0, nq)[j];
+    *a.bar.count = 0u;
+    *a.bar.gen = 0u;
+  }
+}
+
 // which: 0 = the correction pass (each problem in its own precision), 2 = FP64 apply
 template <class HS, class AS>
 const void *batch_kernel_of(int which) {
@@ -2911,7 +3053,10 @@ kq_status batch_graph_prepare(BatchPcg &B, const std::vector<kq_problem *> &hs,
     B.g_err = balloc<int>(B.allocs, 3 * (size_t)nq);
     B.g_resn = balloc<double>(B.allocs, 6 * (size_t)nq);
     B.d_count = balloc<int>(B.allocs, 1);
-    if (!B.gargs || !B.ctl || !B.redout || !B.g_iters || !B.g_err || !B.g_resn || !B.d_count) {
+    B.q_cost = balloc<double>(B.allocs, nq);
+    B.q_cap = balloc<int>(B.allocs, nq);
+    if (!B.gargs || !B.ctl || !B.redout || !B.g_iters || !B.g_err || !B.g_resn || !B.d_count ||
+        !B.q_cost || !B.q_cap) {
       err = "batch graph work space";
       return KQ_ERR_OOM;
     }
@@ -2925,6 +3070,22 @@ kq_status batch_graph_prepare(BatchPcg &B, const std::vector<kq_problem *> &hs,
       err = "batch graph pointers";
       return KQ_ERR_CUDA;
     }
+  }
+  // per-QP cost and team cap for the device-side plan (a batch of more than
+  // KQ_SCHED_MAX_Q QPs keeps the plan made here for the whole capture)
+  {
+    std::vector<double> qc(nq);
+    std::vector<int> qk(nq);
+    for (int q = 0; q < nq; ++q) {
+      qc[q] = unit_cost(hs[q], &B.tune);
+      qk[q] = team_cap(hs[q], &B.tune);
+    }
+    if (cudaMemcpy(B.q_cost, qc.data(), nq * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(B.q_cap, qk.data(), nq * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) {
+      err = "batch graph costs";
+      return KQ_ERR_CUDA;
+    }
+    B.dev_sched = nq <= KQ_SCHED_MAX_Q;
   }
   // teams over the problems still iterating (weight > 0)
   std::vector<int> idx;
@@ -2983,7 +3144,8 @@ kq_status batch_graph_prepare(BatchPcg &B, const std::vector<kq_problem *> &hs,
       err = "batch graph barrier reset";
       return KQ_ERR_CUDA;
     }
-  B.gblocks = tp.nblocks;
+  // a device-planned launch covers every CTA; the plan leaves some idle
+  B.gblocks = (B.dev_sched && tp.nblocks > 0) ? B.G : tp.nblocks;
   if (B.gblocks > 0) {
     if ((e = cudaMemcpy(B.cta_team, tp.cta_team.data(), tp.nblocks * sizeof(int), cudaMemcpyHostToDevice)) != cudaSuccess ||
         (e = cudaMemcpy(B.teams, tp.teams.data(), tp.teams.size() * sizeof(TeamInfo), cudaMemcpyHostToDevice)) != cudaSuccess ||
@@ -3046,6 +3208,12 @@ void batch_graph_pcg_init(BatchPcg &B, int mixed, cudaStream_t s) {
 void batch_graph_pass_setup(BatchPcg &B, int pass, const kq_pcg_opts &o, cudaStream_t s) {
   k_gctl_pass_setup<<<(B.nqp + 255) / 256, 256, 0, s>>>(B.ctl, B.gargs, B.nqp, pass, o.tol, o.inner_tol,
                                                         o.maxit, o.precision == KQ_PREC_MIXED ? o.refine_steps : 0);
+}
+void batch_graph_schedule(BatchPcg &B, cudaStream_t s) {
+  if (!B.dev_sched || B.gblocks == 0) return;
+  k_gctl_schedule<<<1, 1024, schedule_smem(B.nqp, B.G), s>>>(
+      B.ctl, B.gargs, B.nqp, B.G, B.q_cost, B.q_cap, B.cta_team,
+      reinterpret_cast<TeamInfo *>(B.teams), B.team_qps);
 }
 void batch_graph_pass_finish(BatchPcg &B, int pass, int last, int maxit, cudaStream_t s) {
   k_gctl_pass_finish<<<(B.nqp + 255) / 256, 256, 0, s>>>(B.ctl, B.g_iters, B.g_err, B.g_resn, B.redout,
