@@ -59,9 +59,13 @@ enum {
 /* H operator kinds (section 2.2 / section 3.2: H used only through products) */
 enum { KQ_H_DENSE = 0,     /* explicit symmetric n x n, row-major              */
        KQ_H_CSR_LSQ = 1,   /* H = 2 P' diag(w) P, P CSR (rows x n)             */
-       KQ_H_LOWRANK = 2 }; /* H = Z diag(w) Z' + diag(d0), Z dense n x k       */
+       KQ_H_LOWRANK = 2,   /* H = Z diag(w) Z' + diag(d0), Z dense n x k       */
                            /* row-major (w, d0 optional: Z Z' by default); the */
                            /* quasi-Newton form H0 + U W U' of section 2.1     */
+       KQ_H_RBF = 3 };     /* Gaussian-kernel SVM dual (Eq. (6)): H_ij =       */
+                           /* y_i y_j exp(-gamma |x_i - x_j|^2), formed once at */
+                           /* create on the device from the samples X (n x d,  */
+                           /* F64 row-major) and stored as a dense H           */
 /* constraint-matrix kinds (the general rows l <= A x <= u of Eq. (1)) */
 enum { KQ_A_NONE = 0,      /* no general rows                                   */
        KQ_A_DENSE = 1,     /* m x n row-major                                   */
@@ -77,15 +81,18 @@ enum { KQ_PREC_F64 = 0,    /* all FP64                                          
 typedef struct {
   int kind;                /* KQ_H_*                                            */
   int dtype;               /* storage of val/Z/H: KQ_F64, KQ_F32 or KQ_BF16     */
-  int64_t rows;            /* CSR_LSQ: rows of P;  LOWRANK: n;  DENSE: n       */
-  int64_t cols;            /* CSR_LSQ: n;          LOWRANK: k;  DENSE: n       */
+                           /* (RBF: of the formed H; X is always F64)          */
+  int64_t rows;            /* CSR_LSQ: rows of P;  LOWRANK, DENSE, RBF: n      */
+  int64_t cols;            /* CSR_LSQ: n; LOWRANK: k; DENSE: n; RBF: d features*/
   int64_t nnz;             /* CSR_LSQ: nonzeros of P                            */
-  const void *val;         /* DENSE: H; LOWRANK: Z; CSR_LSQ: P values           */
+  const void *val;         /* DENSE: H; LOWRANK: Z; CSR_LSQ: P values; RBF: X   */
   const int32_t *col;      /* CSR_LSQ column indices (sorted not required)     */
   const int64_t *rowptr;   /* CSR_LSQ row pointers (rows+1)                    */
   const double *w;         /* CSR_LSQ row weights (rows), H = 2 P'diag(w)P;    */
-                           /* LOWRANK column weights (k, NULL = all 1)        */
+                           /* LOWRANK column weights (k, NULL = all 1);        */
+                           /* RBF labels y (n, NULL = all 1)                   */
   const double *d0;        /* LOWRANK diagonal H0 (n, NULL = 0)                 */
+  double gamma;            /* RBF kernel width (> 0, finite)                    */
 } kq_hop;
 
 typedef struct {
@@ -124,6 +131,11 @@ typedef struct {
                            /*     iteration once in a CUDA graph and replay it, */
                            /*     every decision taken on the device; 0 = host- */
                            /*     driven launches (default 1)                   */
+  int warm_start;          /* ipm_solve: 1 = each Newton solve after the first  */
+                           /*     starts from the previous Newton direction     */
+                           /*     when that at least halves the FP64 residual,  */
+                           /*     else from zero (section 6 lists warm starts   */
+                           /*     as future work); default 0 (paper: from zero) */
 } kq_ipm_opts;
 
 /* One IPM iteration's record (opts.record = 1): the quantities the paper

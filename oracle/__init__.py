@@ -17,5 +17,6 @@ from .ipm import (  # noqa: F401
     doubly_augmented_matrix, doubly_augmented_rhs, kkt_apply, jacobi_diagonal,
     full_newton_matrix, newton_direct, recover_step, ratio_test, ipm_solve, ipm_iterate,
     pcg_reference, adjoint_solve, unscale_solution, IpmResult, jacobi_scaled_eigenvalues,
+    rbf_hessian,
 )
 from .metrics import kkt_metrics, objective, full_multipliers  # noqa: F401

@@ -127,11 +127,28 @@ def _rownorm(M):
     return r
 
 
+def rbf_hessian(X, y, gamma):
+    """Gaussian-kernel SVM Hessian (Eq. (6) with k(u, v) = exp(-gamma |u - v|^2)):
+    H_ij = y_i y_j exp(-gamma sum_k (X_ik - X_jk)^2), the squared distance
+    summed difference by difference (y = None: all labels 1)."""
+    X = np.asarray(X, dtype=np.float64)
+    n = X.shape[0]
+    H = np.empty((n, n))
+    for i0 in range(0, n, 128):
+        D = X[i0:i0 + 128, None, :] - X[None, :, :]
+        H[i0:i0 + 128] = np.exp(-gamma * np.einsum("ijk,ijk->ij", D, D))
+    if y is not None:
+        y = np.asarray(y, dtype=np.float64)
+        H *= y[:, None] * y[None, :]
+    return H
+
+
 def scale(qp) -> Scaled:
     """Objective scaling by sigma and 2-norm row scaling of A and C."""
     n = qp.n
-    if qp.hkind == "dense":
-        H = qp.H_dense()
+    if qp.hkind in ("dense", "rbf"):
+        # an RBF-kernel H is an explicit dense matrix once formed
+        H = qp.H_dense() if qp.hkind == "dense" else rbf_hessian(qp.X, qp.y, qp.gamma)
         hmax = float(np.max(np.diag(H))) if n else 0.0
     elif qp.hkind == "csr_lsq":
         P = qp.P.astype(np.float64)
@@ -143,8 +160,9 @@ def scale(qp) -> Scaled:
         hmax = float(np.max(np.einsum("ij,ij,j->i", Z, Z, zw) + d0))
     pinf = float(np.max(np.abs(qp.p))) if n else 0.0
     sigma = 1.0 / max(1.0, hmax, pinf)
-    S = Scaled(n=n, hkind=qp.hkind, sigma=sigma, p=sigma * np.asarray(qp.p, float))
-    if qp.hkind == "dense":
+    hk = "dense" if qp.hkind == "rbf" else qp.hkind
+    S = Scaled(n=n, hkind=hk, sigma=sigma, p=sigma * np.asarray(qp.p, float))
+    if hk == "dense":
         S.H = sigma * H
     elif qp.hkind == "csr_lsq":
         S.P = P

@@ -39,6 +39,9 @@ def objective(qp, x):
 def _Hx(qp, x):
     if qp.hkind == "dense":
         return qp.H_dense() @ x
+    if qp.hkind == "rbf":
+        from .ipm import rbf_hessian
+        return rbf_hessian(qp.X, qp.y, qp.gamma) @ x
     if qp.hkind == "csr_lsq":
         P = qp.P.astype(np.float64)
         return 2.0 * (P.T @ (qp.w * (P @ x)))

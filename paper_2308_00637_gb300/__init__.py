@@ -27,7 +27,7 @@ KQ_WARN_PCG_MAXIT, KQ_ERR_IPM_MAXIT, KQ_ERR_TIMEOUT, KQ_ERR_NUMERIC, KQ_ERR_STAT
 STATUS_NAMES = {0: "OK", 1: "ERR_ARG", 2: "ERR_CUDA", 3: "ERR_OOM", 4: "ERR_NOT_CONVEX",
                 5: "WARN_PCG_MAXIT", 6: "ERR_IPM_MAXIT", 7: "ERR_TIMEOUT", 8: "ERR_NUMERIC",
                 9: "ERR_STATE"}
-KQ_H_DENSE, KQ_H_CSR_LSQ, KQ_H_LOWRANK = 0, 1, 2
+KQ_H_DENSE, KQ_H_CSR_LSQ, KQ_H_LOWRANK, KQ_H_RBF = 0, 1, 2, 3
 KQ_A_NONE, KQ_A_DENSE, KQ_A_CSR, KQ_A_ROWS_OF_P = 0, 1, 2, 3
 KQ_F64, KQ_F32, KQ_BF16 = 0, 1, 2
 KQ_PREC_F64, KQ_PREC_MIXED = 0, 1
@@ -36,7 +36,8 @@ KQ_PREC_F64, KQ_PREC_MIXED = 0, 1
 class KqHop(C.Structure):
     _fields_ = [("kind", C.c_int), ("dtype", C.c_int), ("rows", C.c_int64), ("cols", C.c_int64),
                 ("nnz", C.c_int64), ("val", C.c_void_p), ("col", C.c_void_p),
-                ("rowptr", C.c_void_p), ("w", C.c_void_p), ("d0", C.c_void_p)]
+                ("rowptr", C.c_void_p), ("w", C.c_void_p), ("d0", C.c_void_p),
+                ("gamma", C.c_double)]
 
 
 class KqAmat(C.Structure):
@@ -50,7 +51,7 @@ class KqIpmOpts(C.Structure):
                 ("ipm_maxit", C.c_int), ("pcg_tol", C.c_double), ("pcg_maxit", C.c_int),
                 ("precision", C.c_int), ("refine_steps", C.c_int), ("inner_tol", C.c_double),
                 ("timeout_s", C.c_double), ("grid_ctas", C.c_int), ("verbose", C.c_int),
-                ("record", C.c_int), ("graph", C.c_int)]
+                ("record", C.c_int), ("graph", C.c_int), ("warm_start", C.c_int)]
 
 
 class KqIpmIter(C.Structure):
@@ -343,7 +344,7 @@ def _as(a, dtype):
 
 
 def create_from(qp, device_tensors: bool = False, stream=None) -> Handle:
-    """Marshal a problem object (attributes n, hkind, p, H/P/w/Z, akind, A,
+    """Marshal a problem object (attributes n, hkind, p, H/P/w/Z/X, akind, A,
     a_rows, lA, uA, C, b, lx, ux -- the layout of the seeded generators) into
     qp_create.  With ``device_tensors`` the buffers are first moved to the
     current CUDA device (torch), so that qp_create copies device to device."""
@@ -376,6 +377,14 @@ def create_from(qp, device_tensors: bool = False, stream=None) -> Handle:
         H.col = _ptr(buf(qp.P.indices, np.int32))
         H.rowptr = _ptr(buf(qp.P.indptr, np.int64))
         H.w = _ptr(buf(qp.w, np.float64))
+    elif qp.hkind == "rbf":
+        # samples, labels and width; the library forms H (stored as `rbf_dtype`)
+        H.kind, H.rows, H.cols = KQ_H_RBF, n, qp.X.shape[1]
+        H.dtype = {"f64": KQ_F64, "f32": KQ_F32, "bf16": KQ_BF16}[qp.meta.get("rbf_dtype", "f64")]
+        H.val = _ptr(buf(qp.X, np.float64))
+        if getattr(qp, "y", None) is not None:
+            H.w = _ptr(buf(qp.y, np.float64))
+        H.gamma = float(qp.gamma)
     else:
         H.kind, H.dtype, H.rows, H.cols = KQ_H_LOWRANK, KQ_F32, n, qp.Z.shape[1]
         H.val = _ptr(buf(qp.Z, np.float32))

@@ -15,6 +15,12 @@ __device__ __forceinline__ double ld_as_f64(const __nv_bfloat16 *p, int64_t i) {
 }
 __device__ __forceinline__ float ld_as_f32(const double *p, int64_t i) { return (float)p[i]; }
 __device__ __forceinline__ float ld_as_f32(const float *p, int64_t i) { return p[i]; }
+// store a double in the storage type (round to nearest)
+__device__ __forceinline__ void st_from_f64(double *p, int64_t i, double v) { p[i] = v; }
+__device__ __forceinline__ void st_from_f64(float *p, int64_t i, double v) { p[i] = (float)v; }
+__device__ __forceinline__ void st_from_f64(__nv_bfloat16 *p, int64_t i, double v) {
+  p[i] = __double2bfloat16(v);
+}
 __device__ __forceinline__ float ld_as_f32(const __nv_bfloat16 *p, int64_t i) {
   return __bfloat162float(p[i]);
 }

@@ -65,6 +65,48 @@ __global__ void k_dense_diag(int64_t n, int64_t ld, const HS *H, double *d) {
     d[i] = ld_as_f64(H, i * ld + i);
 }
 
+// Gaussian-kernel SVM Hessian (Eq. (6)), formed once:
+// H_ij = y_i y_j exp(-gamma sum_k (X_ik - X_jk)^2) into the padded dense
+// storage (row stride ld).  One 32 x 32 tile of H per CTA of 32 x 8 threads
+// (four entries a thread); 32-feature slabs of the tile's two row blocks of X
+// staged in shared memory; squared differences summed in FP64 in feature
+// order, so H is exactly symmetric and its diagonal is y_i^2.
+template <class HS>
+__global__ void __launch_bounds__(256) k_rbf_build(int64_t n, int64_t d, const double *X,
+                                                   const double *y, double gamma, int64_t ld,
+                                                   HS *H) {
+  __shared__ double xi[32][33], xj[32][33];
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int64_t k0 = 0; k0 < d; k0 += 32) {
+    for (int r = ty; r < 32; r += 8) {
+      const int64_t k = k0 + tx;
+      xi[r][tx] = (i0 + r < n && k < d) ? X[(i0 + r) * d + k] : 0.0;
+      xj[r][tx] = (j0 + r < n && k < d) ? X[(j0 + r) * d + k] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int k = 0; k < 32; ++k) {
+      const double b = xj[tx][k];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const double t = xi[ty + 8 * u][k] - b;
+        acc[u] = fma(t, t, acc[u]);
+      }
+    }
+    __syncthreads();
+  }
+  const int64_t j = j0 + tx;
+  if (j >= n) return;
+  const double yj = y ? y[j] : 1.0;
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int64_t i = i0 + ty + 8 * u;
+    if (i < n) st_from_f64(H, i * ld + j, (y ? y[i] : 1.0) * yj * exp(-gamma * acc[u]));
+  }
+}
+
 // diag(Z diag(zw) Z' + diag(d0))_i = sum_c zw_c Z_ic^2 + d0_i (zw, d0 optional)
 template <class ZS>
 __global__ void k_rownorm2(int64_t rows, int64_t k, const ZS *Z, const double *zw,
@@ -912,6 +954,7 @@ void kq_default_ipm_opts(kq_ipm_opts *o) {
   o->verbose = 0;
   o->record = 0;
   o->graph = 1;
+  o->warm_start = 0;
 }
 
 void kq_default_pcg_opts(kq_pcg_opts *o) {
@@ -956,6 +999,12 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
   } else if (H->kind == KQ_H_DENSE) {
     if (akind == KQ_A_ROWS_OF_P) return kq_fail(nullptr, KQ_ERR_ARG, "ROWS_OF_P needs CSR_LSQ H");
     if (!H->val) return kq_fail(nullptr, KQ_ERR_ARG, "dense H values missing");
+  } else if (H->kind == KQ_H_RBF) {
+    if (akind == KQ_A_ROWS_OF_P) return kq_fail(nullptr, KQ_ERR_ARG, "ROWS_OF_P needs CSR_LSQ H");
+    if (!H->val || H->rows != n || H->cols <= 0 || !(H->gamma > 0.0) || isinf(H->gamma) ||
+        n > (int64_t)65535 * 32 ||
+        (H->dtype != KQ_F64 && H->dtype != KQ_F32 && H->dtype != KQ_BF16))
+      return kq_fail(nullptr, KQ_ERR_ARG, "RBF needs X (n x d, d > 0), finite gamma > 0 and an H storage type");
   } else if (H->kind == KQ_H_LOWRANK) {
     if (akind != KQ_A_NONE && akind != KQ_A_CSR)
       return kq_fail(nullptr, KQ_ERR_ARG, "LOWRANK H supports A = NONE or CSR");
@@ -978,7 +1027,9 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
   h->n = n; h->m = m; h->me = me; h->nkp = n + me + 2 * m;
   DevProb &P = h->P;
   P.n = n; P.m = m; P.me = me; P.nkp = h->nkp;
-  P.hkind = H->kind; P.hdtype = H->dtype; P.akind = akind;
+  // an RBF-kernel H is formed once and then used as a stored dense H
+  P.hkind = H->kind == KQ_H_RBF ? KQ_H_DENSE : H->kind;
+  P.hdtype = H->dtype; P.akind = akind;
   P.adtype = (akind == KQ_A_DENSE || akind == KQ_A_CSR) ? A->dtype : KQ_F64;
   auto fail = [&](kq_status st, const std::string &msg) {
     g_global_err = msg;
@@ -1010,6 +1061,43 @@ kq_status qp_create(kq_handle *out, int64_t n, const kq_hop *H, const double *p,
     if (!P.Hd) return fail(KQ_ERR_OOM, "H");
     if (cudaMemcpy2DAsync((void *)P.Hd, P.hld * es, H->val, n * es, n * es, n, cudaMemcpyDefault, s) != cudaSuccess)
       return fail(KQ_ERR_CUDA, "H upload");
+    if (H->dtype == KQ_F64)
+      k_dense_diag<double><<<NB, NT, 0, s>>>(n, P.hld, (const double *)P.Hd, hdiag);
+    else if (H->dtype == KQ_F32)
+      k_dense_diag<float><<<NB, NT, 0, s>>>(n, P.hld, (const float *)P.Hd, hdiag);
+    else
+      k_dense_diag<__nv_bfloat16><<<NB, NT, 0, s>>>(n, P.hld, (const __nv_bfloat16 *)P.Hd, hdiag);
+  } else if (H->kind == KQ_H_RBF) {
+    // samples and labels are needed only while H is formed
+    P.hld = (n + 7) & ~(int64_t)7;
+    const size_t es = dtype_size(H->dtype);
+    P.Hd = up(nullptr, (size_t)n * P.hld * es);
+    if (!P.Hd) return fail(KQ_ERR_OOM, "H");
+    const int64_t d = H->cols;
+    double *Xd = nullptr, *yd = nullptr;
+    if (cudaMalloc((void **)&Xd, (size_t)n * d * sizeof(double)) != cudaSuccess)
+      return fail(KQ_ERR_OOM, "RBF samples");
+    if (H->w && cudaMalloc((void **)&yd, (size_t)n * sizeof(double)) != cudaSuccess) {
+      cudaFree(Xd);
+      return fail(KQ_ERR_OOM, "RBF labels");
+    }
+    cudaError_t e = cudaMemcpyAsync(Xd, H->val, (size_t)n * d * sizeof(double), cudaMemcpyDefault, s);
+    if (e == cudaSuccess && yd) e = cudaMemcpyAsync(yd, H->w, (size_t)n * sizeof(double), cudaMemcpyDefault, s);
+    if (e == cudaSuccess) {
+      const dim3 grid((unsigned)ceil_div64(n, 32), (unsigned)ceil_div64(n, 32));
+      if (H->dtype == KQ_F64)
+        k_rbf_build<double><<<grid, 256, 0, s>>>(n, d, Xd, yd, H->gamma, P.hld, (double *)P.Hd);
+      else if (H->dtype == KQ_F32)
+        k_rbf_build<float><<<grid, 256, 0, s>>>(n, d, Xd, yd, H->gamma, P.hld, (float *)P.Hd);
+      else
+        k_rbf_build<__nv_bfloat16><<<grid, 256, 0, s>>>(n, d, Xd, yd, H->gamma, P.hld,
+                                                        (__nv_bfloat16 *)P.Hd);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(Xd);
+    if (yd) cudaFree(yd);
+    if (e != cudaSuccess) return fail(KQ_ERR_CUDA, std::string("RBF build: ") + cudaGetErrorString(e));
     if (H->dtype == KQ_F64) k_dense_diag<double><<<NB, NT, 0, s>>>(n, P.hld, (const double *)P.Hd, hdiag);
     else if (H->dtype == KQ_F32) k_dense_diag<float><<<NB, NT, 0, s>>>(n, P.hld, (const float *)P.Hd, hdiag);
     else k_dense_diag<__nv_bfloat16><<<NB, NT, 0, s>>>(n, P.hld, (const __nv_bfloat16 *)P.Hd, hdiag);
@@ -1426,6 +1514,7 @@ kq_status ipm_solve(kq_handle h, const kq_ipm_opts *opts, double *x, double *lam
       rec.mu = mu;
     }
     po.precision = to_f64 ? KQ_PREC_F64 : o.precision;
+    h->warm_next = o.warm_start && it > 1;   // z holds the previous Newton direction
     rc = pcg_solve(h, h->K.rhs, h->z, po, &ps);
     if (h->record) {
       rec.pcg_iters = ps.iters;

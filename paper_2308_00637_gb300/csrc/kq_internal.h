@@ -229,7 +229,8 @@ struct kq_problem {
   long long pcg_launches = 0;   // persistent PCG launches (solve + apply)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   // per-IPM-iteration records (opts.record)
-  bool record = false;          // the current ipm_solve keeps records
+  bool record = false;
+  bool warm_next = false;      // the next pcg_solve starts from the z it is given          // the current ipm_solve keeps records
   bool lz_on = false;           // the next PCG launch writes its alpha, beta
   int lz_steps = 0;             // Lanczos estimates of the last recorded pass
   double lz_min = 0.0, lz_max = 0.0;

@@ -2683,16 +2683,49 @@ kq_status pcg_solve(kq_problem *h, const double *rhs, double *z, const kq_pcg_op
                     kq_pcg_stats *st) {
   const int64_t N = h->P.nkp;
   kq_pcg_stats s{};
+  const bool warm = h->warm_next;   // one solve only
+  h->warm_next = false;
   const double bn = dev_norm(h, rhs, N);
-  KQ_CUDA(h, cudaMemsetAsync(z, 0, N * sizeof(double), h->stream));
   if (!(bn > 0.0)) {
+    KQ_CUDA(h, cudaMemsetAsync(z, 0, N * sizeof(double), h->stream));
     s.status = (bn == 0.0) ? KQ_OK : KQ_ERR_NUMERIC;
     if (st) *st = s;
     return s.status == KQ_OK ? KQ_OK : kq_fail(h, KQ_ERR_NUMERIC, "rhs has NaN/Inf");
   }
   double *res = h->tmp, *dz = h->zref;
-  KQ_CUDA(h, cudaMemcpyAsync(res, rhs, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   double resn = bn;
+  bool cold = !warm;
+  if (warm) {
+    // warm start from the direction already in z: res = rhs - K z in FP64
+    float ms = 0.f;
+    const kq_status rc0 = pcg_apply(h, z, dz, KQ_PREC_F64, &ms);
+    if (rc0 != KQ_OK) return rc0;
+    s.kernel_ms += ms;
+    s.kernel_ms_f64 += ms;
+    s.products_f64 += 1;
+    s.products += 1;
+    s.launches_f64 += 1;
+    const int nb = 256;
+    k_axpy_res<<<nb, 256, 0, h->stream>>>(N, rhs, dz, res, h->red);
+    ++h->launches;
+    k_final_sum<<<1, 256, 0, h->stream>>>(nb, h->red, h->red_out);
+    ++h->launches;
+    KQ_CUDA(h, cudaMemcpyAsync(h->h_red, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    KQ_CUDA(h, cudaStreamSynchronize(h->stream));
+    resn = sqrt(h->h_red[0]);
+    if (!(resn <= 0.5 * bn)) {
+      cold = true;   // the old direction does not help (or is not finite)
+      resn = bn;
+    } else if (resn <= o.tol * bn) {
+      s.rel_res = resn / bn;
+      if (st) *st = s;
+      return KQ_OK;
+    }
+  }
+  if (cold) {
+    KQ_CUDA(h, cudaMemsetAsync(z, 0, N * sizeof(double), h->stream));
+    KQ_CUDA(h, cudaMemcpyAsync(res, rhs, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  }
   int total = 0;
   const int mixed = o.precision == KQ_PREC_MIXED;
   const int max_passes = (mixed ? o.refine_steps : 0) + 3;

@@ -16,7 +16,9 @@ structures:
 * ``lowrank`` : H = Z W Z^T + H0 with Z a dense n x k matrix, W = diag(zw)
                 (default I) and H0 = diag(d0) (default 0): the linear-kernel SVM
                 dual (Z Z^T), or a quasi-Newton (BFGS) Hessian of the form
-                H0 + U W U^T.
+                H0 + U W U^T;
+* ``rbf``     : H_ij = y_i y_j exp(-gamma ||x_i - x_j||^2), the Gaussian-kernel
+                SVM dual, given by its samples X (n x d), labels y and gamma.
 
 A constraint matrix A is either dense, a CSR matrix, or a subset of the rows of
 P (``a_rows``), which is how dose-limit constraints reuse the dose matrix.
@@ -41,7 +43,7 @@ class QPData:
     """One convex QP (Eq. (1)), in original (unscaled) units."""
 
     n: int
-    hkind: str                      # 'dense' | 'csr_lsq' | 'lowrank'
+    hkind: str                      # 'dense' | 'csr_lsq' | 'lowrank' | 'rbf'
     p: np.ndarray                   # linear term, float64 (n,)
     H: Optional[np.ndarray] = None  # dense H (float64 values), n x n
     P: Optional[sp.csr_matrix] = None   # csr_lsq: float32 CSR, rows x n
@@ -49,6 +51,9 @@ class QPData:
     Z: Optional[np.ndarray] = None      # lowrank: float32 n x k
     zw: Optional[np.ndarray] = None     # lowrank: column weights W (None = 1)
     d0: Optional[np.ndarray] = None     # lowrank: diagonal H0 (None = 0)
+    X: Optional[np.ndarray] = None      # rbf: samples, float64 n x d
+    y: Optional[np.ndarray] = None      # rbf: labels (+-1), float64 n
+    gamma: float = 0.0                  # rbf: kernel width
     akind: str = "none"             # 'none' | 'dense' | 'csr' | 'rows_of_p'
     A: object = None                # dense ndarray (float64) or csr (float32)
     a_rows: Optional[np.ndarray] = None  # rows_of_p: int32 row ids into P
@@ -92,6 +97,8 @@ class QPData:
         if self.hkind == "csr_lsq":
             P = self.P.astype(np.float64)
             return np.asarray((2.0 * (P.T @ sp.diags(self.w) @ P)).todense())
+        if self.hkind == "rbf":
+            return rbf_matrix(self.X, self.y, self.gamma)
         Z = self.Z.astype(np.float64)
         zw = np.ones(Z.shape[1]) if self.zw is None else np.asarray(self.zw, float)
         d0 = np.zeros(self.n) if self.d0 is None else np.asarray(self.d0, float)
@@ -99,7 +106,7 @@ class QPData:
 
     def objective(self, x: np.ndarray) -> float:
         """1/2 x^T H x + p^T x, evaluated from the operator's structure."""
-        if self.hkind == "dense":
+        if self.hkind in ("dense", "rbf"):
             Hx = self.H_dense() @ x
         elif self.hkind == "csr_lsq":
             P = self.P.astype(np.float64)
@@ -301,6 +308,37 @@ def svm_qp(N: int = 50_000, dim: int = 256, cbox: float = 1.0, seed: int = 2) ->
     X = (0.5 * y[:, None] + rng.standard_normal((N, dim))).astype(np.float32)
     Z = (y[:, None].astype(np.float32) * X).astype(np.float32)
     return QPData(n=N, hkind="lowrank", p=_full(N, -1.0), Z=Z, akind="none",
+                  C=y[None, :].copy(), b=np.zeros(1), lx=_full(N, 0.0),
+                  ux=_full(N, cbox), meta={"seed": seed, "y": y})
+
+
+# ---------------------------------------------------------------------------
+# Gaussian-kernel SVM dual (Eq. (6) with k(u, v) = exp(-gamma ||u - v||^2)):
+# samples and labels as in svm_qp (two Gaussians, means +-0.5 in every
+# feature), gamma = 1/dim by default.
+#   min 1/2 a^T (Y K Y) a - e^T a   s.t.  y^T a = 0,  0 <= a <= cbox.
+# Draw order: label permutation, X noise.
+# ---------------------------------------------------------------------------
+def rbf_matrix(X: np.ndarray, y: Optional[np.ndarray], gamma: float) -> np.ndarray:
+    """H = diag(y) K diag(y), K_ij = exp(-gamma ||x_i - x_j||^2), float64."""
+    X = np.asarray(X, dtype=np.float64)
+    sq = np.einsum("ij,ij->i", X, X)
+    d2 = np.maximum(sq[:, None] + sq[None, :] - 2.0 * (X @ X.T), 0.0)
+    np.fill_diagonal(d2, 0.0)
+    K = np.exp(-gamma * d2)
+    if y is not None:
+        K = K * np.outer(y, y)
+    return K
+
+
+def rbf_svm_qp(N: int = 600, dim: int = 10, cbox: float = 1.0, gamma: Optional[float] = None,
+               seed: int = 51) -> QPData:
+    rng = np.random.default_rng(seed)
+    y = np.ones(N)
+    y[rng.permutation(N)[: N // 2]] = -1.0
+    X = 0.5 * y[:, None] + rng.standard_normal((N, dim))
+    g = 1.0 / dim if gamma is None else float(gamma)
+    return QPData(n=N, hkind="rbf", p=_full(N, -1.0), X=X, y=y, gamma=g, akind="none",
                   C=y[None, :].copy(), b=np.zeros(1), lx=_full(N, 0.0),
                   ux=_full(N, cbox), meta={"seed": seed, "y": y})
 

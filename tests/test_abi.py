@@ -64,3 +64,35 @@ def test_create_without_device_fails_loudly(lib):
     import paper_2308_00637_gb300 as kq
     with pytest.raises(kq.KQError):
         kq.create_from(qpgen.dense_qp(8, 4, seed=1))
+
+
+def test_struct_layouts_match_header(tmp_path):
+    """Every ctypes mirror of a header struct has the C compiler's size and
+    field offsets (a field added on one side only would shift every field
+    after it and be read as garbage)."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    import paper_2308_00637_gb300 as m
+    structs = {"kq_hop": m.KqHop, "kq_amat": m.KqAmat, "kq_ipm_opts": m.KqIpmOpts,
+               "kq_ipm_iter": m.KqIpmIter, "kq_ipm_stats": m.KqIpmStats,
+               "kq_pcg_opts": m.KqPcgOpts, "kq_pcg_stats": m.KqPcgStats,
+               "kq_qp_desc": m.KqQpDesc, "kq_batch_stats": m.KqBatchStats}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "kktqp.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} %zu\\n", sizeof({cname}));')
+        for f in py._fields_:
+            lines.append(f'printf("{cname}.{f[0]} %zu\\n", offsetof({cname}, {f[0]}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([gcc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for cname, py in structs.items():
+        assert int(got[cname]) == ctypes.sizeof(py), cname
+        for f in py._fields_:
+            assert int(got[f"{cname}.{f[0]}"]) == getattr(py, f[0]).offset, (cname, f[0])

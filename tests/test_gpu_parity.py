@@ -37,6 +37,10 @@ PROBLEMS = {
     "lowrank_csrA_eq": lambda: qpgen.svm_qp_general(),
     # quasi-Newton Hessian H0 + U W U' (section 2.1) with sparse dose-like rows
     "lowrank_bfgs": lambda: qpgen.bfgs_qp(800, 10, 60, 15, seed=43),
+    # Gaussian-kernel SVM dual (Eq. (6)): H formed on the device from X, y, gamma
+    # (n = 500 is not a multiple of the 32 x 32 build tile; d = 37 spans two
+    # 32-feature slabs)
+    "rbf_svm": lambda: qpgen.rbf_svm_qp(500, 37, seed=52),
 }
 
 
@@ -282,3 +286,20 @@ def test_initial_point_worked_example(kq):
     assert bufs["lam_lx"][2] == 0.0 and bufs["lam_ux"][1] == 0.0
     assert np.allclose(bufs["lam_e"], 0.0)
     kq.qp_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["dense_eq", "csr", "lowrank_bfgs", "rbf_svm"])
+def test_warm_start_matches_oracle(kq, name):
+    """Warm-started Newton solves (opts.warm_start: each PCG starts from the
+    previous Newton direction when that halves the FP64 residual) take the
+    same IPM path to the same point: objective within 1e-6 of the oracle's,
+    the same final mu, and the termination test met."""
+    qp = PROBLEMS[name]()
+    res = _oracle_result(name)
+    rc, st, out = kq.solve(qp, kq.default_ipm_opts(warm_start=1))
+    _, st0, _ = kq.solve(qp, kq.default_ipm_opts())
+    print(name, "PCG iterations warm", st.pcg_iters, "cold", st0.pcg_iters)
+    f_gpu, f_ref = qp.objective(out["x"]), qp.objective(res.x)
+    assert abs(f_gpu - f_ref) <= 1e-6 * (1 + abs(f_ref)), (f_gpu, f_ref, st.as_dict())
+    assert st.mu_final == pytest.approx(res.mu)
+    assert st.res_norm < st.mu_final

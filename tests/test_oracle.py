@@ -533,3 +533,38 @@ def test_infeasibilities_split_the_residual_norm():
     assert du ** 2 == pytest.approx(15.725, rel=1e-13)
     assert co ** 2 == pytest.approx(9.7, rel=1e-13)
     assert pr ** 2 + du ** 2 + co ** 2 == pytest.approx(WORKED_NORM2, rel=1e-13)
+
+
+def test_rbf_hessian_library_distances_and_invariants():
+    """The Gaussian-kernel Hessian of the SVM dual (Eq. (6)): squared
+    distances from scipy's cdist agree; a hand case (|x1 - x2|^2 = 25,
+    gamma = 0.02, labels +-1) gives H12 = -exp(-0.5); H is symmetric positive
+    semidefinite with unit diagonal (y_i^2 exp(0))."""
+    from scipy.spatial.distance import cdist
+    H2 = oracle.rbf_hessian(np.array([[0.0, 0.0], [3.0, 4.0]]), np.array([1.0, -1.0]), 0.02)
+    assert H2[0, 1] == pytest.approx(-np.exp(-0.5), rel=1e-15)
+    assert H2[1, 0] == H2[0, 1] and H2[0, 0] == 1.0 and H2[1, 1] == 1.0
+    qp = qpgen.rbf_svm_qp(150, 7, seed=3)
+    H = oracle.rbf_hessian(qp.X, qp.y, qp.gamma)
+    Hl = np.exp(-qp.gamma * cdist(qp.X, qp.X, "sqeuclidean")) * np.outer(qp.y, qp.y)
+    assert np.max(np.abs(H - Hl)) <= 1e-13
+    assert np.array_equal(H, H.T) and np.all(np.diag(H) == 1.0)
+    assert np.min(np.linalg.eigvalsh(H)) >= -1e-10
+    # the generator's own Gram-form matrix (used for objectives) agrees too
+    assert np.max(np.abs(H - qp.H_dense())) <= 1e-12
+
+
+def test_rbf_svm_two_samples_closed_form():
+    """Two samples of opposite labels at distance r: y'a = 0 forces
+    a1 = a2 = a and the dual objective is a^2 (1 - k) - 2a with
+    k = exp(-gamma r^2), so a* = 1 / (1 - k) while the box is inactive."""
+    gamma, r = 1.0, 1.0
+    y = np.array([1.0, -1.0])
+    qp = qpgen.QPData(n=2, hkind="rbf", p=np.full(2, -1.0), X=np.array([[0.0], [r]]), y=y,
+                      gamma=gamma, akind="none", C=y[None, :].copy(), b=np.zeros(1),
+                      lx=np.zeros(2), ux=np.full(2, 10.0))
+    res = oracle.ipm_solve(qp)
+    astar = 1.0 / (1.0 - np.exp(-gamma * r * r))
+    assert res.status == "converged"
+    assert np.max(np.abs(res.x - astar)) <= 1e-5 * astar
+    assert qp.objective(res.x) == pytest.approx(-astar, rel=1e-6)
