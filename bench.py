@@ -276,12 +276,16 @@ def batch_line(kq, qps, prec, graph, peak, peak_src, head):
 def other_configs(kq, qpgen):
     """Time-to-1e-6 of the other configurations in both forms (one warm-up
     solve, one timed), for the record next to the benchmark line: c0 (dense
-    n = 200), c2 (linear SVM dual), c4 (dose QP at 1/4 size), and the first
-    32 QPs of the 512-QP batch with n <= 1024 (graph form)."""
+    n = 200), c2 (linear SVM dual), c4 (dose QP at 1/4 size), the RBF-kernel
+    SVM dual of a1a's shape, and the first 32 QPs of the 512-QP batch with
+    n <= 1024 (graph form)."""
     import numpy as np
     out = {}
     for name, mk in (("c0_dense_n200", qpgen.config0), ("c2_svm_50k", qpgen.config2),
-                     ("c4_dose_50k_x_5k", qpgen.config4)):
+                     ("c4_dose_50k_x_5k", qpgen.config4),
+                     # Gaussian-kernel SVM dual of a1a's shape (Table 1: 1605
+                     # variables, one equality; H formed on the device)
+                     ("rbf_svm_1605x123", lambda: qpgen.rbf_svm_qp(1605, 123, seed=51))):
         qp = mk()
         d = {}
         for prec, form in ((kq.KQ_PREC_F64, "f64"), (kq.KQ_PREC_MIXED, "mixed")):

@@ -51,9 +51,11 @@ kq_status batch_pcg(kq_batch b, const std::vector<int> &act, const kq_pcg_opts &
   }
   const int mixed = o.precision == KQ_PREC_MIXED;
   const int max_passes = (mixed ? o.refine_steps : 0) + 3;
-  // per QP: FP32 correction passes while they pay (a pass that does not halve
+  // per QP: FP32 correction passes only for QPs whose products are large
+  // enough (batch_f32_pays), and while they pay (a pass that does not halve
   // the true residual hands that QP to FP64 passes)
-  std::vector<int> fp32_ok(k, mixed ? 1 : 0);
+  std::vector<int> fp32_ok(k, 0);
+  for (int j = 0; j < k; ++j) fp32_ok[j] = mixed && batch_f32_pays(hs[act[j]]);
   std::vector<double> resn_before(k, 0.0);
   for (int pass = 0; pass < max_passes; ++pass) {
     std::vector<int> idx;
@@ -262,11 +264,13 @@ kq_status ipm_solve_batch_graph_on(kq_batch b, const kq_ipm_opts &o, double *con
   kq_status rc = batch_graph_prepare(B, hs, weight, e);   // allocates the control words
   if (rc != KQ_OK) return bfail(b, rc, e);
   std::vector<QpCtl> ctl(nq);
-  for (QpCtl &c : ctl) {
+  for (int q = 0; q < nq; ++q) {
+    QpCtl &c = ctl[q];
     c = QpCtl{};
     c.active = 1;
     c.mu = o.mu0;
     c.status = KQ_ERR_IPM_MAXIT;
+    c.f32_pays = batch_f32_pays(hs[q]);
   }
   if (cudaMemcpy(B.ctl, ctl.data(), nq * sizeof(QpCtl), cudaMemcpyHostToDevice) != cudaSuccess)
     return bfail(b, KQ_ERR_CUDA, "batch graph: control words");

@@ -64,6 +64,7 @@ struct QpCtl {
   int fp32_ok;       // FP32 correction passes still pay for this QP
   int used;          // PCG iterations of the current Newton solve
   int w_prev;        // PCG iterations of the previous Newton solve (team costs)
+  int f32_pays;      // MIXED: this QP's products are large enough for FP32 passes
   int kexp;          // mu = mu0 10^-kexp
   int ipm_iters;
   int status;        // KQ_OK once converged; an error code if a step failed
@@ -335,6 +336,11 @@ kq_status batch_graph_launch(BatchPcg &B, const kq_problem *h0, int which, cudaS
 void batch_graph_pcg_init(BatchPcg &B, int mixed, cudaStream_t s);
 void batch_graph_pass_setup(BatchPcg &B, int pass, const kq_pcg_opts &o, cudaStream_t s);
 void batch_graph_schedule(BatchPcg &B, cudaStream_t s);
+// MIXED in a batch: FP32 correction passes only for a QP whose product reads
+// at least a quarter of the L2 (smaller products are latency-bound, FP32
+// arithmetic saves nothing there and costs PCG iterations)
+constexpr double KQ_BATCH_F32_MIN_BYTES = 32.0e6;
+bool batch_f32_pays(const kq_problem *h);
 void batch_graph_pass_finish(BatchPcg &B, int pass, int last, int maxit, cudaStream_t s);
 void batch_graph_step(BatchPcg &B, double gamma, cudaStream_t s);
 void batch_graph_mu_rule(BatchPcg &B, double mu0, double mu_tol, cudaStream_t s);

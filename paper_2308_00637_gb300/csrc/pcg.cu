@@ -1972,6 +1972,15 @@ double unit_cost(const kq_problem *h, const BatchTune *tune) {
   return hb * h->n * h->n + ab * h->m * h->n + 64.0 * h->nkp;
 }
 
+bool batch_f32_pays(const kq_problem *h) {
+  const double hb = h->P.hdtype == KQ_F64 ? 8.0 : (h->P.hdtype == KQ_F32 ? 4.0 : 2.0);
+  const double ab = h->P.adtype == KQ_F64 ? 8.0 : 4.0;
+  // KQ_BATCH_F32_MIN_BYTES overrides the threshold (0: FP32 passes for every QP)
+  const char *ev = getenv("KQ_BATCH_F32_MIN_BYTES");
+  const double thr = ev ? atof(ev) : KQ_BATCH_F32_MIN_BYTES;
+  return hb * h->n * h->n + ab * h->m * h->n >= thr;
+}
+
 // largest team of a batched problem: two rows of H, A, C per warp of the
 // team, the CTAs its slot buffer holds, and the tuned cap of its size bucket
 int team_cap(const kq_problem *h, const BatchTune *tune) {
@@ -2808,7 +2817,7 @@ __global__ void k_gctl_pcg_init(QpCtl *ctl, int nq, int mixed) {
     c.pcg_done = c.active ? 0 : 1;
     if (c.used > 0) c.w_prev = c.used;
     c.used = 0;
-    c.fp32_ok = mixed;
+    c.fp32_ok = mixed && c.f32_pays;
     c.resn = 0.0;
     c.bnorm = 0.0;
     c.ran = 0;

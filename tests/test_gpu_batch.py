@@ -49,7 +49,10 @@ def _check_against_oracle(kq, b, k, qp, x, tag):
 
 
 @pytest.mark.parametrize("prec", [0, 1], ids=["f64", "mixed"])
-def test_small_batch_against_oracle(kq, prec):
+def test_small_batch_against_oracle(kq, prec, monkeypatch):
+    # mixed: FP32 correction passes for every QP (by default only QPs whose
+    # products read >= 32 MB take them; these are far smaller)
+    monkeypatch.setenv("KQ_BATCH_F32_MIN_BYTES", "0")
     sizes = qpgen.batch_sizes(16, 16, 400, size_seed=3)
     qps = [qpgen.batch_qp(k, n) for k, n in enumerate(sizes)]
     b = kq.qp_create_batch(qps)
@@ -123,11 +126,13 @@ def test_c3_largest_against_oracle(kq, prec):
 
 
 @pytest.mark.parametrize("prec", [1, 0], ids=["mixed", "f64"])
-def test_graph_replay_matches_host_driven(kq, prec):
+def test_graph_replay_matches_host_driven(kq, prec, monkeypatch):
     """The lock-step IPM iteration captured once in a CUDA graph and
     replayed, every decision (pass precision, PCG stop, step lengths, mu
-    rule, done) taken on the device, gives the host-driven solver's solution
-    and the oracle's; the graph is captured again only when QPs finish."""
+    rule, done) and the teams of every pass made on the device, gives the
+    host-driven solver's solution and the oracle's; the graph is captured
+    again only when QPs finish.  Mixed: FP32 passes for every QP."""
+    monkeypatch.setenv("KQ_BATCH_F32_MIN_BYTES", "0")
     sizes = qpgen.batch_sizes(24, 16, 600, size_seed=11)
     qps = [qpgen.batch_qp(k, n) for k, n in enumerate(sizes)]
     res = {}
