@@ -185,18 +185,65 @@ def oracle_steps(nwarm: int, nsteps: int, threads: int):
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+# The CPU restatement of the paper's own design (FP64 C++/OpenMP, matrix-free
+# Eq. (9), Jacobi-PCG): a fixed number of PCG iterations on the first Newton
+# system of the benchmark workload (the oracle supplies the system).
+RESTATEMENT_CODE = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import qpgen, cpu_restatement as cr
+from oracle import ipm as I
+qp = qpgen.config1()
+S = I.scale(qp)
+st = I.initial_point(S)
+r = I.residuals(S, st, 1.0)
+dg, D, r1, r2 = I.reduced_system(S, st, r, 1.0)
+rhs = I.doubly_augmented_rhs(S, D, r1, r2)
+diag = I.jacobi_diagonal(S, dg, D)
+sysc = cr.System(S.P, S.w2, S.A, S.L, S.U, dg, D)
+sysc.pcg(diag, rhs, tol=0.0, maxit=3)
+t0 = time.perf_counter()
+_, it, rel = sysc.pcg(diag, rhs, tol=0.0, maxit={iters})
+dt = time.perf_counter() - t0
+print(json.dumps({{"iters": it, "seconds": dt, "bytes_per_apply": sysc.bytes_per_apply(),
+                  "threads": cr.threads()}}))
+"""
+
+
+def restatement_pcg(iters: int, threads: int):
+    """PCG iterations per second of the CPU restatement on the host cores."""
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads))
+    out = subprocess.run([sys.executable, "-c", RESTATEMENT_CODE.format(root=ROOT, iters=iters)],
+                         capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    ips = r["iters"] / r["seconds"]
+    return {"pcg_iters_per_s": ips, "gbs": r["bytes_per_apply"] * ips / 1e9,
+            "threads": r["threads"], "iters": r["iters"], "seconds": r["seconds"],
+            "sample": (f"{r['iters']} FP64 Jacobi-PCG iterations (fixed count) of the CPU "
+                       f"restatement (C++/OpenMP, matrix-free Eq. (9)) on the first Newton "
+                       f"system of the full 200k x 20k dose QP; gbs = bytes one apply reads "
+                       f"({r['bytes_per_apply'] / 1e6:.0f} MB: P and A twice) x iterations/s")}
+
+
 def cpu_baseline_line(nsteps=3):
     model, cores = host_cpu()
     nit = oracle_iters_per_solve()
     r = oracle_steps(0, nsteps, cores)
     per = sum(r["times"]) / len(r["times"])
+    try:
+        rest = restatement_pcg(100, cores)
+    except Exception as e:   # reported, not fatal
+        rest = {"error": str(e)[-300:]}
     return {"value": per * nit, "unit": "s", "cores": cores, "kind": "oracle",
             "cpu": model,
             "sample": (f"IPM iterations {r['iters'][0]}-{r['iters'][-1]} of the FP64 oracle's own "
                        f"trajectory on the full 200k x 20k dose QP (direct banded-Schur Newton "
                        f"solves, BLAS on {cores} threads), {per:.2f} s each; scaled by the "
                        f"{nit} IPM iterations of the oracle's full solve of this workload"),
-            "s_per_ipm_iteration": per, "ipm_iterations_per_solve": nit}
+            "s_per_ipm_iteration": per, "ipm_iterations_per_solve": nit,
+            "pcg_restatement": rest}
 
 
 # ---------------------------------------------------------------- reference arm
@@ -247,20 +294,24 @@ def batch_bytes_per_product(q) -> float:
     return hb * q.n * q.n + ab * q.m * q.n
 
 
-def batch_line(kq, qps, prec, graph, peak, peak_src, head):
+def batch_line(kq, qps, prec, graph, peak, peak_src, head, ipm_maxit=200):
     """Solve a batch once and describe it: time, convergence, and the
     effective bandwidth of its products (algorithmic bytes x each QP's PCG
     iterations / device time of the solve's launches -- the whole replayed
-    iteration in the graph form, so a lower bound there)."""
+    iteration in the graph form, so a lower bound there).  With ipm_maxit
+    below Algorithm 1's N the line states the cost of that many lock-step
+    IPM iterations."""
     import numpy as np
     b = kq.qp_create_batch(qps)
     xs = [np.zeros(q.n) for q in qps]
-    rc, status, st = kq.ipm_solve_batch(b, kq.default_ipm_opts(precision=prec, graph=graph), xs)
+    rc, status, st = kq.ipm_solve_batch(b, kq.default_ipm_opts(precision=prec, graph=graph,
+                                                               ipm_maxit=ipm_maxit), xs)
     per = [kq.qp_batch_qp_stats(b, i) for i in range(len(qps))]
     kq.qp_batch_destroy(b)
     byts = sum(batch_bytes_per_product(q) * it for q, (_, it) in zip(qps, per))
     gbs = byts / (st.pcg_kernel_ms * 1e-3) / 1e9 if st.pcg_kernel_ms > 0 else None
-    return dict(head, **{"time_to_1e-6_s": st.time_s, "converged": st.converged,
+    return dict(head, **{"time_to_1e-6_s" if ipm_maxit >= 200 else "time_s": st.time_s,
+                         "ipm_maxit": ipm_maxit, "converged": st.converged,
                          "status": int(rc), "ipm_iters_max": st.ipm_iters_max,
                          "pcg_iters": int(st.pcg_iters), "pcg_maxit_hits": st.pcg_maxit_hits,
                          "device_ms": st.pcg_kernel_ms, "graph_captures": st.graph_captures,
@@ -366,11 +417,17 @@ def run_other(args):
     sizes = qpgen.batch_sizes(nqp, 64, hi, size_seed=5 if args.workload == "batch128" else 0)
     qps = [qpgen.batch_qp(k, n, light=True) for k, n in enumerate(sizes)]
     peak, peak_src = read_peaks()
-    forms = ((kq.KQ_PREC_MIXED, 1, "batched mixed, graph"), (kq.KQ_PREC_F64, 1, "batched f64, graph"),
-             (kq.KQ_PREC_MIXED, 0, "batched mixed, host-driven"))
-    for prec, graph, name in forms:
+    forms = {"mixed-graph": (kq.KQ_PREC_MIXED, 1, "batched mixed, graph"),
+             "f64-graph": (kq.KQ_PREC_F64, 1, "batched f64, graph"),
+             "mixed-host": (kq.KQ_PREC_MIXED, 0, "batched mixed, host-driven"),
+             "f64-host": (kq.KQ_PREC_F64, 0, "batched f64, host-driven")}
+    pick = list(forms) if args.batch_form == "all" else [args.batch_form]
+    for key in pick:
+        prec, graph, name = forms[key]
         emit(batch_line(kq, qps, prec, graph, peak, peak_src,
-                        {"workload": args.workload, "form": name, "nqp": nqp}))
+                        {"workload": args.workload, "form": name, "nqp": nqp,
+                         "sum_4n2_bytes": sum(batch_bytes_per_product(q) for q in qps)},
+                        ipm_maxit=args.ipm_maxit))
     if args.sequential:
         tot, its = 0.0, 0
         for q in qps:
@@ -402,6 +459,12 @@ def main():
                          "per form (plain FP64 / mixed / batched) on the other configurations")
     ap.add_argument("--nqp", type=int, default=0,
                     help="batch workloads: number of QPs (default 128 / 512)")
+    ap.add_argument("--batch-form", default="all",
+                    choices=["all", "mixed-graph", "f64-graph", "mixed-host", "f64-host"],
+                    help="batch workloads: which form(s) to run")
+    ap.add_argument("--ipm-maxit", type=int, default=200,
+                    help="batch workloads: stop after this many lock-step IPM iterations "
+                         "(the line then gives their cost, not a time-to-1e-6)")
     ap.add_argument("--sequential", action="store_true",
                     help="batch workloads: also time plain FP64 one QP at a time")
     args = ap.parse_args()
