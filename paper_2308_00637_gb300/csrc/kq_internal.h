@@ -337,9 +337,10 @@ void batch_graph_pcg_init(BatchPcg &B, int mixed, cudaStream_t s);
 void batch_graph_pass_setup(BatchPcg &B, int pass, const kq_pcg_opts &o, cudaStream_t s);
 void batch_graph_schedule(BatchPcg &B, cudaStream_t s);
 // MIXED in a batch: FP32 correction passes only for a QP whose product reads
-// at least a quarter of the L2 (smaller products are latency-bound, FP32
-// arithmetic saves nothing there and costs PCG iterations)
-constexpr double KQ_BATCH_F32_MIN_BYTES = 32.0e6;
+// at least the L2's capacity.  Smaller products are latency-bound in a batch,
+// and the lock-step passes put a QP's FP32 correction passes behind the other
+// QPs' FP64 pass, so the FP32 passes cost more than they save there.
+constexpr double KQ_BATCH_F32_MIN_BYTES = 128.0e6;
 bool batch_f32_pays(const kq_problem *h);
 void batch_graph_pass_finish(BatchPcg &B, int pass, int last, int maxit, cudaStream_t s);
 void batch_graph_step(BatchPcg &B, double gamma, cudaStream_t s);

@@ -51,7 +51,7 @@ def _check_against_oracle(kq, b, k, qp, x, tag):
 @pytest.mark.parametrize("prec", [0, 1], ids=["f64", "mixed"])
 def test_small_batch_against_oracle(kq, prec, monkeypatch):
     # mixed: FP32 correction passes for every QP (by default only QPs whose
-    # products read >= 32 MB take them; these are far smaller)
+    # products read >= 128 MB take them; these are far smaller)
     monkeypatch.setenv("KQ_BATCH_F32_MIN_BYTES", "0")
     sizes = qpgen.batch_sizes(16, 16, 400, size_seed=3)
     qps = [qpgen.batch_qp(k, n) for k, n in enumerate(sizes)]
