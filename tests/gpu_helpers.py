@@ -53,3 +53,31 @@ def relerr(a, b):
     a, b = np.asarray(a), np.asarray(b)
     d = np.max(np.abs(a - b)) if a.size else 0.0
     return d / (1e-300 + max(np.max(np.abs(b)) if b.size else 0.0, 1e-300))
+
+
+def kkt_abs_apply(S, dg, D, v):
+    """|K| |v| for the K of Eq. (9), matrix-free from |H|, |B| and D (every
+    term of each entry's sum taken by its magnitude): the per-entry scale
+    that rounding errors of K v are bounded by."""
+    import scipy.sparse as sp
+    n = S.n
+    ax, al = np.abs(v[:n]), np.abs(v[n:])
+    if S.hkind == "dense":
+        hv = np.abs(S.H) @ ax
+    elif S.hkind == "csr_lsq":
+        Pa = abs(S.P)
+        hv = Pa.T @ (np.abs(S.w2) * (Pa @ ax))
+    else:
+        Za = np.abs(S.Z)
+        hv = Za @ (np.abs(S.zw) * (Za.T @ ax)) + np.abs(S.d0) * ax
+    Aa = abs(S.A) if sp.issparse(S.A) else np.abs(S.A)
+    Ca = np.abs(S.C)
+    Av = Aa @ ax
+    t = np.concatenate([Ca @ ax, Av[S.L], Av[S.U]])
+    y = 2.0 * t / D + al
+    me, nl = S.me, len(S.L)
+    z = np.zeros(Aa.shape[0])
+    np.add.at(z, S.L, y[me:me + nl])
+    np.add.at(z, S.U, y[me + nl:])
+    top = hv + np.abs(dg) * ax + Ca.T @ y[:me] + np.asarray(Aa.T @ z).ravel()
+    return np.concatenate([top, t + D * al])
