@@ -453,6 +453,9 @@ def main():
     ap.add_argument("--no-others", action="store_true",
                     help="skip the other configurations' record on the benchmark line")
     ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--warm-start", type=int, default=0,
+                    help="1: each Newton solve's PCG starts from the previous direction "
+                         "(opts.warm_start); 0: from zero, as the paper")
     ap.add_argument("--workload", default="c1",
                     choices=["c1", "c0", "c2", "c4", "batch128", "batch512"],
                     help="c1 (default) is the benchmark; the others print one timing line "
@@ -496,7 +499,7 @@ def main():
 
     qp = qpgen.config1()
     prec = kq.KQ_PREC_MIXED if args.precision == "mixed" else kq.KQ_PREC_F64
-    opts = kq.default_ipm_opts(precision=prec)
+    opts = kq.default_ipm_opts(precision=prec, warm_start=int(args.warm_start))
     h = kq.create_from(qp, device_tensors=True)
     n, m = h.n, h.m
     dev = {k: torch.zeros(s, dtype=torch.float64, device="cuda")
@@ -641,7 +644,7 @@ def main():
             "dtype": "f32-matvec/f64" if prec == kq.KQ_PREC_MIXED else "f64",
             "data": "synthetic (seeded generator, seed 1)",
             "config": dict(CONFIG, rows=qp.P.shape[0], n=qp.n, nnz=qp.P.nnz, dose_limit_rows=m,
-                           precision=args.precision,
+                           precision=args.precision, warm_start=bool(args.warm_start),
                            parallelism="replicas" if world > 1 else "single-gpu"),
             "ipm_iters": s0.ipm_iters, "pcg_iters": int(s0.pcg_iters),
             "pcg_products": int(s0.pcg_products), "pcg_iters_f64": int(s0.pcg_iters_f64),
