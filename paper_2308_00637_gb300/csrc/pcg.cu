@@ -26,6 +26,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <vector>
+#include <type_traits>
 
 namespace {
 
@@ -248,6 +249,89 @@ __device__ __forceinline__ void row_dot2(const S *r0, const S *r1, bool two, con
   }
 }
 
+// ---- double-float products (FP64-class accuracy on the FP32 pipe)
+// GB300 retires FP32 multiply-adds at ~64x its FP64 rate.  Where the matrix
+// is stored in bf16 or f32 (exact in FP32), an FP64 product p = M v is formed
+// as follows: v splits into v_h + v_l (two floats), each term m v_h is an
+// exact float pair (the rounded product and its FMA residual), and every
+// lane accumulates in a float pair (s_h, s_l) whose high part takes the
+// rounded products through an error-free two-sum (Knuth) and whose low part
+// collects the residuals, the m v_l terms and the two-sum errors.  Relative
+// accuracy about 2^-48 per term (FP64: 2^-53), far inside the 1e-7 PCG
+// tolerance.  The explicit _rn intrinsics keep the compiler from contracting
+// a product into the following sum, which would break the error-free steps.
+struct DFAcc {
+  float h = 0.f, l = 0.f;
+  __device__ __forceinline__ void add_prod(float m, float vh, float vl) {
+    const float p = __fmul_rn(m, vh);
+    const float e = __fmaf_rn(m, vh, -p);
+    const float q = __fmaf_rn(m, vl, e);
+    const float s = __fadd_rn(h, p);
+    const float bp = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+    l = __fadd_rn(l, __fadd_rn(err, q));
+    h = s;
+  }
+  __device__ __forceinline__ void add(float oh, float ol) {
+    const float s = __fadd_rn(h, oh);
+    const float bp = __fsub_rn(s, h);
+    const float err = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bp)), __fsub_rn(oh, bp));
+    l = __fadd_rn(l, __fadd_rn(err, ol));
+    h = s;
+  }
+  __device__ __forceinline__ void warp_reduce() {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_xor_sync(0xffffffffu, h, o), ol = __shfl_xor_sync(0xffffffffu, l, o);
+      add(oh, ol);
+    }
+  }
+  __device__ __forceinline__ double value() const { return (double)h + (double)l; }
+};
+
+__device__ __forceinline__ void df_split(double v, float &vh, float &vl) {
+  vh = __double2float_rn(v);
+  vl = __double2float_rn(v - (double)vh);
+}
+
+// dots of two rows (bf16 or f32 storage) with the window held as float pairs
+template <class S>
+__device__ __forceinline__ void row_dot2_df(const S *r0, const S *r1, bool two, const float *ph,
+                                            const float *pl, int64_t n, bool vec, int lane,
+                                            double &d0, double &d1) {
+  DFAcc a0, a1;
+  if (vec) {
+#pragma unroll 2
+    for (int64_t j = 8 * lane; j < n; j += 256) {
+      float v0[8], v1[8];
+      Load8<S, float>::run(r0 + j, v0);
+      if (two) Load8<S, float>::run(r1 + j, v1);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float xh = ph[j + k], xl = pl[j + k];
+        a0.add_prod(v0[k], xh, xl);
+        if (two) a1.add_prod(v1[k], xh, xl);
+      }
+    }
+  } else {
+    for (int64_t j = lane; j < n; j += 32) {
+      const float xh = ph[j], xl = pl[j];
+      a0.add_prod(ld_as_f32(r0, j), xh, xl);
+      if (two) a1.add_prod(ld_as_f32(r1, j), xh, xl);
+    }
+  }
+  a0.warp_reduce();
+  a1.warp_reduce();
+  d0 = a0.value();
+  d1 = two ? a1.value() : 0.0;
+}
+
+template <class HS, class AS, class T>
+struct DenseDF {
+  static constexpr bool value = sizeof(T) == 8 && !std::is_same<HS, double>::value &&
+                                std::is_same<AS, float>::value;
+};
+
 template <class HS, class AS>
 struct OpDense {
   // vcta / vG: this CTA's rank and the number of CTAs working on the problem
@@ -276,9 +360,18 @@ struct OpDense {
     const int64_t md = P.akind == KQ_A_DENSE ? m : 0;
     const bool colpass = n >= (a.colpass_min_n > 0 ? a.colpass_min_n : 512) && md > 0 &&
                          a.coefA != nullptr && avec;
+    constexpr bool DF = DenseDF<HS, AS, T>::value;
+    // DF: the window as float pairs in the same bytes (high parts, then low)
+    float *pwh = reinterpret_cast<float *>(pw), *pwl = pwh + a.win_cap;
+    auto pw_at = [&](int64_t j) -> T {
+      if constexpr (DF) return (T)((double)pwh[j] + (double)pwl[j]);
+      else return pw[j];
+    };
     double pq = write_owned_p(a, ysrc, pold, pnew, beta, vb, ve);
     for (int64_t j = tid; j < npad; j += blockDim.x) {
-      pw[j] = j < n ? (T)(ldcg(ysrc + j) + beta * ldcg(pold + j)) : (T)0;
+      const double v = j < n ? ldcg(ysrc + j) + beta * ldcg(pold + j) : 0.0;
+      if constexpr (DF) df_split(v, pwh[j], pwl[j]);
+      else pw[j] = (T)v;
       acc[j] = (T)0;
     }
     __syncthreads();
@@ -289,7 +382,15 @@ struct OpDense {
       const int64_t r2 = row + GW;
       const bool two = r2 < n;
       T d0, d1;
-      row_dot2<HS, T>(Hd + row * hld, Hd + (two ? r2 : row) * hld, two, pw, n, hvec, lane, d0, d1);
+      if constexpr (DF) {
+        double e0, e1;
+        row_dot2_df<HS>(Hd + row * hld, Hd + (two ? r2 : row) * hld, two, pwh, pwl, n, hvec, lane,
+                        e0, e1);
+        d0 = e0;
+        d1 = e1;
+      } else {
+        row_dot2<HS, T>(Hd + row * hld, Hd + (two ? r2 : row) * hld, two, pw, n, hvec, lane, d0, d1);
+      }
       if (lane == 0) {
         d0 *= (T)P.hscale;
         atomicAdd(acc + row, d0);
@@ -338,7 +439,15 @@ struct OpDense {
       const int64_t a2 = ai + GW;
       const bool two = a2 < md;
       T d0, d1;
-      row_dot2<AS, T>(Ad + ai * ald, Ad + (two ? a2 : ai) * ald, two, pw, n, avec, lane, d0, d1);
+      if constexpr (DF) {
+        double e0, e1;
+        row_dot2_df<AS>(Ad + ai * ald, Ad + (two ? a2 : ai) * ald, two, pwh, pwl, n, avec, lane,
+                        e0, e1);
+        d0 = e0;
+        d1 = e1;
+      } else {
+        row_dot2<AS, T>(Ad + ai * ald, Ad + (two ? a2 : ai) * ald, two, pw, n, avec, lane, d0, d1);
+      }
       arow(ai, d0);
       if (two) arow(a2, d1);
     }
@@ -347,7 +456,7 @@ struct OpDense {
     for (int64_t e = e0; e < me; e += GW) {
       const double *cr = P.Cd + e * n;
       T dot = (T)0;
-      for (int64_t j = lane; j < n; j += 32) dot += (T)cr[j] * pw[j];
+      for (int64_t j = lane; j < n; j += 32) dot += (T)cr[j] * pw_at(j);
       dot = warp_sum(dot);
       const double t = (double)dot;
       const double pe = ldcg(ysrc + n + e) + beta * ldcg(pold + n + e);
@@ -377,6 +486,28 @@ struct OpDense {
         const int64_t blk = task % nblk, rs = task / nblk;
         const int64_t c0 = blk * 256 + 8 * lane;
         const int64_t a0 = rs * rows_per, a1 = (a0 + rows_per < md) ? a0 + rows_per : md;
+        if constexpr (DF) {
+          // A' columns in double-float: the coefficient splits, A is f32
+          if (c0 < n) {
+            DFAcc s8[8];
+            for (int64_t ai = a0; ai < a1; ++ai) {
+              const double cfd = __ldcg(a.coefA + ai);
+              if (cfd == 0.0) continue;
+              float ch, cl;
+              df_split(cfd, ch, cl);
+              float v[8];
+              Load8<AS, float>::run(Ad + ai * ald + c0, v);
+#pragma unroll
+              for (int k = 0; k < 8; ++k) s8[k].add_prod(v[k], ch, cl);
+            }
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const double v = s8[k].value();
+              if (c0 + k < n && v != 0.0) atomicAdd(accg + c0 + k, (T)v);
+            }
+          }
+          continue;
+        }
         T s8[8];
 #pragma unroll
         for (int k = 0; k < 8; ++k) s8[k] = (T)0;

@@ -42,6 +42,10 @@ PROBLEMS = {
     # (n = 500 is not a multiple of the 32 x 32 build tile; d = 37 spans two
     # 32-feature slabs)
     "rbf_svm": lambda: qpgen.rbf_svm_qp(500, 37, seed=52),
+    # bf16 H and f32 A (the batched QPs' storage): FP64 products in
+    # double-float arithmetic; n = 700 >= 512 takes the column pass for A'
+    "dense_bf16": lambda: qpgen.batch_qp(3, 300),
+    "dense_bf16_colpass": lambda: qpgen.batch_qp(5, 700),
 }
 
 
