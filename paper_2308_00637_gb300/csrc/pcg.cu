@@ -358,9 +358,11 @@ struct OpDense {
     const bool avec = (ald % 8 == 0) && ((reinterpret_cast<uintptr_t>(Ad) & 15) == 0);
     // general rows handled here only when A is dense (a CSR A has its own pass)
     const int64_t md = P.akind == KQ_A_DENSE ? m : 0;
-    const bool colpass = n >= (a.colpass_min_n > 0 ? a.colpass_min_n : 512) && md > 0 &&
-                         a.coefA != nullptr && avec;
     constexpr bool DF = DenseDF<HS, AS, T>::value;
+    // double-float products always take the column pass: the row-wise A'
+    // scatter would need FP64 shared-memory atomics per element
+    const bool colpass = (DF || n >= (a.colpass_min_n > 0 ? a.colpass_min_n : 512)) && md > 0 &&
+                         a.coefA != nullptr && avec;
     // DF: the window as float pairs in the same bytes (high parts, then low)
     float *pwh = reinterpret_cast<float *>(pw), *pwl = pwh + a.win_cap;
     auto pw_at = [&](int64_t j) -> T {
@@ -1057,24 +1059,6 @@ __host__ __device__ inline RowsLayout rows_layout(int rws, int nw, int a_cap, in
   return L;
 }
 
-// FP32 -> FP64 on the integer pipe (IEEE-754 binary32 -> binary64 re-encoding:
-// sign kept, exponent rebased by 1023 - 127 = 896, mantissa shifted left by
-// 29).  Exact for every normal number and zero; subnormals, infinities and
-// NaN take the hardware conversion.  The SM's FP64 unit is narrow, and the
-// hardware conversion runs on it.
-__device__ __forceinline__ double f32_to_f64(float f) {
-  const uint32_t b = __float_as_uint(f);
-  const uint32_t e = (b >> 23) & 0xffu;
-  const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
-  if (e == 0u && (b & 0x7fffffu) == 0u) return __longlong_as_double((long long)sign);
-  if (e == 0u || e == 0xffu) return (double)f;
-  return __longlong_as_double((long long)(sign | ((uint64_t)(e + 896u) << 52) |
-                                          ((uint64_t)(b & 0x7fffffu) << 29)));
-}
-template <class T> __device__ __forceinline__ T from_f32(float f);
-template <> __device__ __forceinline__ float from_f32<float>(float f) { return f; }
-template <> __device__ __forceinline__ double from_f32<double>(float f) { return f32_to_f64(f); }
-
 // L2 bulk prefetch; the caller passes a 16-byte aligned address
 __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   if (bytes >= 16)
@@ -1149,6 +1133,27 @@ struct OpCsrRows {
     __syncthreads();
   }
 
+  // FP64 products in double-float: one row's scatter of u P_r into the warp's
+  // accumulator held as float pairs (columns distinct)
+  static __device__ __forceinline__ void scatter_df(float2 *accw, const float4 &v, const int4 &c,
+                                                    double u, bool act) {
+    if (act) {
+      float uh, ul;
+      df_split(u, uh, ul);
+      const float2 a0 = accw[c.x], a1 = accw[c.y], a2 = accw[c.z], a3 = accw[c.w];
+      DFAcc t0{a0.x, a0.y}, t1{a1.x, a1.y}, t2{a2.x, a2.y}, t3{a3.x, a3.y};
+      t0.add_prod(v.x, uh, ul);
+      t1.add_prod(v.y, uh, ul);
+      t2.add_prod(v.z, uh, ul);
+      t3.add_prod(v.w, uh, ul);
+      accw[c.x] = make_float2(t0.h, t0.l);
+      accw[c.y] = make_float2(t1.h, t1.l);
+      accw[c.z] = make_float2(t2.h, t2.l);
+      accw[c.w] = make_float2(t3.h, t3.l);
+    }
+    __syncwarp();
+  }
+
   // one row's scatter into the warp's accumulator (columns distinct)
   template <class T>
   static __device__ __forceinline__ void scatter(T *accw, const T (&v)[4], const int4 &c, T u,
@@ -1207,7 +1212,8 @@ struct OpCsrRows {
       if (lane < x1.len4) { v1 = __ldcs(a.rval4 + x1.off4 + lane); c1 = __ldcs(a.rcol2 + x1.off4 + lane); }
     };
     T pqt = (T)0;
-    // one pair of rows: dots with the window, coefficients, scatter
+    // one pair of rows: dots with the window, coefficients, scatter (FP32
+    // products; FP64 products take process_df below)
     auto process = [&](int ii, const RowSlot &s0, const RowSlot &s1, const float4 &v0,
                        const float4 &v1, const uint2 &p0, const uint2 &p1) {
       const int4 c0 = make_int4((int)(p0.x & 0xffffu), (int)(p0.x >> 16), (int)(p0.y & 0xffffu),
@@ -1216,15 +1222,9 @@ struct OpCsrRows {
                                 (int)(p1.y >> 16));
       const bool has1 = ii + 1 < nr;
       const bool act0 = lane < s0.len4, act1 = lane < s1.len4;
-      // FP64 products: the low part of the FP32-split row weight
-      float w0lo = 0.f, w1lo = 0.f;
-      if constexpr (sizeof(T) == 8) {
-        w0lo = __ldg(a.rw2lo + r0 + ii);
-        if (has1) w1lo = __ldg(a.rw2lo + r0 + ii + 1);
-      }
-      // values in the product type, converted once for the dot and the scatter
-      const T x0[4] = {from_f32<T>(v0.x), from_f32<T>(v0.y), from_f32<T>(v0.z), from_f32<T>(v0.w)};
-      const T x1[4] = {from_f32<T>(v1.x), from_f32<T>(v1.y), from_f32<T>(v1.z), from_f32<T>(v1.w)};
+      const float w0lo = 0.f, w1lo = 0.f;
+      const T x0[4] = {(T)v0.x, (T)v0.y, (T)v0.z, (T)v0.w};
+      const T x1[4] = {(T)v1.x, (T)v1.y, (T)v1.z, (T)v1.w};
       T d0 = (T)0, d1 = (T)0;
       if (act0) d0 = x0[0] * pw[c0.x] + x0[1] * pw[c0.y] + x0[2] * pw[c0.z] + x0[3] * pw[c0.w];
       if (act1) d1 = x1[0] * pw[c1.x] + x1[1] * pw[c1.y] + x1[2] * pw[c1.z] + x1[3] * pw[c1.w];
@@ -1243,6 +1243,48 @@ struct OpCsrRows {
       if (lane == 0) pqt += u0 * d0 + u1 * d1;
       scatter<T>(accw, x0, c0, u0, act0);
       scatter<T>(accw, x1, c1, u1, act1);
+    };
+    // FP64 products in double-float (window and accumulators as float pairs,
+    // the FP32 matrix values exact): dots, coefficients in FP64, scatter
+    auto process_df = [&](int ii, const RowSlot &s0, const RowSlot &s1, const float4 &v0,
+                          const float4 &v1, const uint2 &p0, const uint2 &p1) {
+      const float2 *pw2 = reinterpret_cast<const float2 *>(pw);
+      float2 *acc2w = reinterpret_cast<float2 *>(accw);
+      const int4 c0 = make_int4((int)(p0.x & 0xffffu), (int)(p0.x >> 16), (int)(p0.y & 0xffffu),
+                                (int)(p0.y >> 16));
+      const int4 c1 = make_int4((int)(p1.x & 0xffffu), (int)(p1.x >> 16), (int)(p1.y & 0xffffu),
+                                (int)(p1.y >> 16));
+      const bool has1 = ii + 1 < nr;
+      const bool act0 = lane < s0.len4, act1 = lane < s1.len4;
+      const float w0lo = __ldg(a.rw2lo + r0 + ii), w1lo = has1 ? __ldg(a.rw2lo + r0 + ii + 1) : 0.f;
+      DFAcc q0, q1;
+      if (act0) {
+        const float2 g0 = pw2[c0.x], g1 = pw2[c0.y], g2 = pw2[c0.z], g3 = pw2[c0.w];
+        q0.add_prod(v0.x, g0.x, g0.y);
+        q0.add_prod(v0.y, g1.x, g1.y);
+        q0.add_prod(v0.z, g2.x, g2.y);
+        q0.add_prod(v0.w, g3.x, g3.y);
+      }
+      if (act1) {
+        const float2 g0 = pw2[c1.x], g1 = pw2[c1.y], g2 = pw2[c1.z], g3 = pw2[c1.w];
+        q1.add_prod(v1.x, g0.x, g0.y);
+        q1.add_prod(v1.y, g1.x, g1.y);
+        q1.add_prod(v1.z, g2.x, g2.y);
+        q1.add_prod(v1.w, g3.x, g3.y);
+      }
+      q0.warp_reduce();
+      q1.warp_reduce();
+      const T d0 = (T)q0.value(), d1 = (T)q1.value();
+      const RowDesc rd0{0, s0.a, s0.w2, w0lo}, rd1{0, s1.a, s1.w2, w1lo};
+      const T u0 = OpCsrStaged::row_coef<T>(a, rd0, d0, ysrc, pold, beta, alo, na, arho, acs, aDl,
+                                            aDu, apl, apu, afl, lane, pqt);
+      T u1 = (T)0;
+      if (has1)
+        u1 = OpCsrStaged::row_coef<T>(a, rd1, d1, ysrc, pold, beta, alo, na, arho, acs, aDl, aDu,
+                                      apl, apu, afl, lane, pqt);
+      if (lane == 0) pqt += u0 * d0 + u1 * d1;
+      scatter_df(acc2w, v0, c0, (double)u0, act0);
+      scatter_df(acc2w, v1, c1, (double)u1, act1);
     };
     int i = 2 * warp;
     const int stp = 2 * nw;
@@ -1322,7 +1364,14 @@ struct OpCsrRows {
       ld_data(sb0, sb1, vb0, vb1, cb0, cb1);
       for (int j = tid; j < wlen; j += blockDim.x) {
         const int c = lo + j;
-        pw[j] = (T)(ldcg(ysrc + c) + beta * ldcg(pold + c));
+        const double v = ldcg(ysrc + c) + beta * ldcg(pold + c);
+        if constexpr (sizeof(T) == 8) {
+          float h, l;
+          df_split(v, h, l);
+          reinterpret_cast<float2 *>(pw)[j] = make_float2(h, l);
+        } else {
+          pw[j] = (T)v;
+        }
       }
       for (int k = tid; k < na; k += blockDim.x) {
         const int ai = alo + k;
@@ -1339,7 +1388,8 @@ struct OpCsrRows {
       uint2 cc0, cc1;
       ld_slots(i + 3 * stp, sd0, sd1);
       ld_data(sc0, sc1, vc0, vc1, cc0, cc1);
-      process(i, sa0, sa1, va0, va1, ca0, ca1);
+      if constexpr (sizeof(T) == 8) process_df(i, sa0, sa1, va0, va1, ca0, ca1);
+      else process(i, sa0, sa1, va0, va1, ca0, ca1);
       sa0 = sb0; sa1 = sb1; sb0 = sc0; sb1 = sc1; sc0 = sd0; sc1 = sd1;
       va0 = vb0; va1 = vb1; ca0 = cb0; ca1 = cb1;
       vb0 = vc0; vb1 = vc1; cb0 = cc0; cb1 = cc1;
@@ -1347,18 +1397,21 @@ struct OpCsrRows {
     __syncthreads();
     // sum the private copies into the global accumulator; zero them
     if constexpr (sizeof(T) == 8) {
-      double2 *acc2 = reinterpret_cast<double2 *>(acc);
+      // the private copies hold float pairs (two columns per 16 bytes)
+      float4 *accp = reinterpret_cast<float4 *>(acc);
       const int ws2 = a.rws >> 1;
       for (int j2 = tid; j2 < ws2; j2 += blockDim.x) {
-        double2 t = make_double2(0.0, 0.0);
+        DFAcc t0, t1;
         for (int w = 0; w < nw; ++w) {
-          const double2 x = acc2[(size_t)w * ws2 + j2];
-          t.x += x.x; t.y += x.y;
-          acc2[(size_t)w * ws2 + j2] = make_double2(0.0, 0.0);
+          const float4 x = accp[(size_t)w * ws2 + j2];
+          t0.add(x.x, x.y);
+          t1.add(x.z, x.w);
+          accp[(size_t)w * ws2 + j2] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        const double tx = t0.value(), ty = t1.value();
         const int c = 2 * j2;
-        if (c < wlen && t.x != 0.0) atomicAdd(reinterpret_cast<double *>(accg) + lo + c, t.x);
-        if (c + 1 < wlen && t.y != 0.0) atomicAdd(reinterpret_cast<double *>(accg) + lo + c + 1, t.y);
+        if (c < wlen && tx != 0.0) atomicAdd(reinterpret_cast<double *>(accg) + lo + c, tx);
+        if (c + 1 < wlen && ty != 0.0) atomicAdd(reinterpret_cast<double *>(accg) + lo + c + 1, ty);
       }
       (void)ok;
       return pq + (double)pqt;
