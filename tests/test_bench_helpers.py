@@ -4,6 +4,7 @@ import json
 import os
 
 import numpy as np
+import pytest
 
 import bench
 import qpgen
@@ -40,3 +41,24 @@ def test_peak_source():
         assert src == "measured" and peak > 1000
     else:
         assert src == "fallback" and peak == 6800.0
+
+
+def test_dose_kkt_matches_the_oracle_metric():
+    """The bench's restated acceptance measure for the dose QP equals the
+    oracle's (the GPU arm of the bench does not call the oracle)."""
+    import numpy as np
+    import oracle
+    import qpgen
+    from oracle.metrics import full_multipliers
+    qp = qpgen.dose_qp(3000, 300, 30, 40, 150, seed=8)
+    res = oracle.ipm_solve(qp)
+    lam = full_multipliers(res.scaled, res.lam, qp)
+    ref = oracle.kkt_metrics(qp, res.x, *lam)
+    got = bench.dose_kkt(qp, res.x, *lam[:4])
+    for k in ("primal_rel", "dual_rel", "kkt_rel", "objective"):
+        assert got[k] == pytest.approx(ref[k], rel=1e-12, abs=1e-300), k
+    # a perturbed point: both measures move together
+    x2 = res.x + 1e-3
+    ref2 = oracle.kkt_metrics(qp, x2, *lam)
+    got2 = bench.dose_kkt(qp, x2, *lam[:4])
+    assert got2["kkt_rel"] == pytest.approx(ref2["kkt_rel"], rel=1e-12)
