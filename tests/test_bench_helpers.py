@@ -62,3 +62,14 @@ def test_dose_kkt_matches_the_oracle_metric():
     ref2 = oracle.kkt_metrics(qp, x2, *lam)
     got2 = bench.dose_kkt(qp, x2, *lam[:4])
     assert got2["kkt_rel"] == pytest.approx(ref2["kkt_rel"], rel=1e-12)
+
+
+def test_oracle_solve_estimate_counts_the_setup_once():
+    """A full oracle solve = the step that ran the set-up with the first
+    IPM iteration + (iterations - 1) x the plain iteration time."""
+    r = {"times": [10.0, 3.0, 3.0], "iters": [1, 2, 3], "warm_times": []}
+    total, first, per = bench.oracle_solve_estimate(r, 29)
+    assert (total, first, per) == (10.0 + 28 * 3.0, 10.0, 3.0)
+    r = {"times": [3.0, 5.0], "iters": [4, 5], "warm_times": [12.0, 3.0, 3.0]}
+    total, first, per = bench.oracle_solve_estimate(r, 29)
+    assert (total, first, per) == (12.0 + 28 * 4.0, 12.0, 4.0)
