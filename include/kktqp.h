@@ -74,7 +74,10 @@ enum { KQ_A_NONE = 0,      /* no general rows                                   
 /* storage types */
 enum { KQ_F64 = 0, KQ_F32 = 1, KQ_BF16 = 2 };
 /* arithmetic of the K products inside PCG */
-enum { KQ_PREC_F64 = 0,    /* all FP64                                          */
+enum { KQ_PREC_F64 = 0,    /* FP64 vectors, dots, diagonal and step; FP64-class */
+                           /* products: double-float on the FP32 pipe where the */
+                           /* matrix data is exact in FP32 (~2^-48 per term),   */
+                           /* native FP64 otherwise                             */
        KQ_PREC_MIXED = 1 };/* FP32 matvec + FP32 accumulation; FP64 dots,
                               diagonal, step and FP64 residual refinement       */
 
