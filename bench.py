@@ -245,6 +245,8 @@ def cpu_baseline_line(nsteps=3):
     total, first, per = oracle_solve_estimate(r, nit)
     try:
         rest = restatement_pcg(100, cores)
+        one = restatement_pcg(20, 1)
+        rest["one_thread"] = {k: one[k] for k in ("pcg_iters_per_s", "gbs", "iters", "seconds")}
     except Exception as e:   # reported, not fatal
         rest = {"error": str(e)[-300:]}
     return {"value": total, "unit": "s", "cores": cores, "kind": "oracle",
